@@ -1,0 +1,222 @@
+/*
+ * pf.h -- C ABI of the GB300 resampling library (libpf.so).
+ *
+ * Resampling stage of the bootstrap particle filter as defined in Murray,
+ * "GPU acceleration of the particle filter: the Metropolis resampler":
+ * given P unnormalised weights, redraw P particles with replacement, using
+ * the weights as unnormalised probabilities (Section 1, step 4), by one of
+ * the four schemes of Figure 1 -- multinomial, stratified, systematic,
+ * Metropolis -- and copy the chosen particles' states (the ancestor gather).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Weights are given as FP32 log-weights lw[i]; w_i = exp(lw_i) up to a
+ *    common factor.  -inf is a legal log-weight (a zero weight, never
+ *    selected by the cumulative schemes).  NaN or +inf is a domain error.
+ *  - Outputs are ANCESTORS a_j in [0, P), 0-based (Section 2: offspring and
+ *    ancestors are interchangeable; o_i = #{j : a_j = i}).
+ *  - Cumulative schemes select, for a position t in [0, W), the smallest i
+ *    with c_i > t, where c_i = w_0 + ... + w_i and W = c_{P-1}.
+ *  - All array arguments are DEVICE pointers on the current CUDA device,
+ *    owned by the caller, and must stay valid until the stream reaches the
+ *    call.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *  - Every call is asynchronous and stream-ordered.  Argument errors are
+ *    returned synchronously and nothing is enqueued.  Errors found on the
+ *    device (NaN/+inf log-weight, all weights zero, a bounded wait that ran
+ *    out) are recorded in a per-stream device status word, read and cleared
+ *    by pf_get_device_status(); the outputs of that call are then
+ *    unspecified.
+ *  - The library keeps one workspace per (device, stream), grown on demand
+ *    (a synchronous allocation); pf_reserve() pre-sizes it so that later
+ *    calls allocate nothing (required before capturing calls into a CUDA
+ *    graph).  Calls on the same stream share that workspace; calls on
+ *    different streams may run concurrently.
+ *  - Randomness: Philox-4x32-10 (Salmon et al., SC'11) with key = (seed mod
+ *    2^32, seed div 2^32) and counter (c0, c1, filter, tag); filter = 0 for
+ *    the single-filter calls and f for filter f of a batched call; tag 1
+ *    systematic, 2 stratified, 3 multinomial, 4 Metropolis.  Draw j of an
+ *    element stream is word j%4 of counter (j/4, 0, filter, tag).  Metropolis
+ *    chain i, steps b and b+1 (b even), uses counter (i, b/2, filter, 4) whose
+ *    words are (proposal_b, uniform_b, proposal_{b+1}, uniform_{b+1}).
+ *    Uniforms: u23(x) = (2*(x>>9)+1)*2^-24 (systematic, stratified,
+ *    Metropolis), u32(x) = (2x+1)*2^-33 (multinomial); proposals
+ *    j = floor(x*P/2^32).  Every call is therefore a pure function of its
+ *    inputs and seed.
+ *  - Arithmetic: FP32 log-weights and per-element work; each tile's weights
+ *    are taken relative to a power of two near its maximum, so tiles combine
+ *    by exact binary scaling; per-tile sums are compensated FP32 pairs and the
+ *    inter-tile carries FP64.  Results agree with an FP64 evaluation of the
+ *    same definitions except at decisions whose uniform lies within ~1e-6
+ *    (relative) of a cumulative-weight or weight-ratio threshold.
+ */
+#ifndef PF_H_
+#define PF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pf_status {
+    PF_OK = 0,
+    PF_ERR_INVALID = 1, /* bad argument (null pointer, size out of range, misalignment) */
+    PF_ERR_DOMAIN = 2,  /* NaN or +inf log-weight, or every weight zero */
+    PF_ERR_TIMEOUT = 3, /* a bounded device-side wait ran out (see pf_set_wait_limit_ns) */
+    PF_ERR_CUDA = 4,    /* a CUDA runtime call failed */
+    PF_ERR_NOMEM = 5    /* workspace allocation failed, or growth needed during graph capture */
+} pf_status;
+
+/* Resampler kinds for pf_resample_batched. */
+enum {
+    PF_MULTINOMIAL = 0,
+    PF_STRATIFIED = 1,
+    PF_SYSTEMATIC = 2,
+    PF_METROPOLIS = 3
+};
+
+/* Largest P accepted by every call. */
+#define PF_MAX_PARTICLES 2147483647LL
+
+/*
+ * Systematic resampler (Figure 1c; Kitagawa 1996; Section 2).
+ * One uniform u (stream tag 1, draw 0); a_j = smallest i with
+ * c_i > (j + u) W / P, j = 0..P-1.  Output is non-decreasing and every
+ * particle gets floor(P w_i/W) or ceil(P w_i/W) offspring.
+ *   logw      [P] float, 16-byte aligned      (in)
+ *   P         1 <= P <= PF_MAX_PARTICLES
+ *   B         ignored
+ *   seed      Philox key
+ *   ancestors [P] int32, 16-byte aligned      (out)
+ * Errors: PF_ERR_INVALID for null or misaligned pointers or P out of range;
+ * device status PF_ERR_DOMAIN for NaN/+inf or all -inf log-weights.
+ */
+pf_status pf_resample_systematic(const float* logw, int64_t P, int B, uint64_t seed,
+                                 int32_t* ancestors, void* stream);
+
+/*
+ * Stratified resampler (Figure 1b, Section 2).  Stratum j draws its own
+ * uniform u_j (stream tag 2, draw j); a_j = smallest i with
+ * c_i > (j + u_j) W / P.  Output is non-decreasing.  Arguments and errors as
+ * pf_resample_systematic.
+ */
+pf_status pf_resample_stratified(const float* logw, int64_t P, int B, uint64_t seed,
+                                 int32_t* ancestors, void* stream);
+
+/*
+ * Multinomial resampler (Figure 1a; binary search, Section 3).  P i.i.d.
+ * uniforms u_j (stream tag 3, draw j, u32 conversion); a_j = smallest i with
+ * c_i > u_j W.  Output is in draw order (not sorted).  Arguments and errors as
+ * pf_resample_systematic; the workspace holds a P-float cumulative array.
+ */
+pf_status pf_resample_multinomial(const float* logw, int64_t P, int B, uint64_t seed,
+                                  int32_t* ancestors, void* stream);
+
+/*
+ * Metropolis resampler (Figure 1d; Section 2).  Chain i starts at k = i and
+ * takes B steps; step b proposes j uniformly over all P indices (a proposal of
+ * k itself changes nothing) and moves to it when lw_j >= lw_k or when
+ * u_b < exp(lw_j - lw_k).  a_i is the chain's final state.  No sum of weights
+ * is formed.
+ *   B > 0   number of steps;  B == 0 gives a_i = i;
+ *   B < 0   B is chosen on the device from the bound of Eqs. 1-5 with
+ *           eps = 0.01 and the actual w_max (see pf_metropolis_B), capped at
+ *           2^24 steps; this adds one reduction pass over logw.
+ * Arguments otherwise as pf_resample_systematic.  Zero weights everywhere are
+ * not an error here (the chains simply move to their proposals); NaN/+inf is.
+ */
+pf_status pf_resample_metropolis(const float* logw, int64_t P, int B, uint64_t seed,
+                                 int32_t* ancestors, void* stream);
+
+/*
+ * Ancestor gather (Section 1, step 4: the redrawn sample set).
+ *   dst row j  <-  src row ancestors[j],   j = 0..P_dst-1
+ *   src       [P_src][row_bytes] bytes, row-major   (in)
+ *   ancestors [P_dst] int32                         (in)
+ *   dst       [P_dst][row_bytes] bytes, row-major   (out; must not overlap src)
+ * row_bytes must be a positive multiple of 4.  16-byte alignment of src, dst
+ * and row_bytes selects 128-bit accesses; otherwise narrower ones are used.
+ * An ancestor outside [0, P_src) leaves that row untouched and sets device
+ * status PF_ERR_INVALID.
+ */
+pf_status pf_gather(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* ancestors,
+                    int64_t P_dst, void* dst, void* stream);
+
+/*
+ * Effective sample size (Section 3 quotes ESS/P for its weight sets; the
+ * standard form is used): ess_out[0] = (sum w)^2 / sum w^2, and, if
+ * log_sum_out is not NULL, log_sum_out[0] = log sum_i exp(lw_i).
+ *   logw        [P] float, 16-byte aligned      (in)
+ *   ess_out     [1] float  (device)             (out)
+ *   log_sum_out [1] double (device) or NULL     (out)
+ * Device status PF_ERR_DOMAIN for NaN/+inf or all -inf log-weights.
+ */
+pf_status pf_ess(const float* logw, int64_t P, float* ess_out, double* log_sum_out, void* stream);
+
+/*
+ * Batched resampling of F independent filters (the many filters of particle
+ * MCMC, Section 1) in one persistent launch over a work queue.
+ *   kind      PF_MULTINOMIAL, PF_STRATIFIED, PF_SYSTEMATIC or PF_METROPOLIS
+ *   logw      concatenated log-weights; filter f owns logw[offsets[f] .. offsets[f+1])
+ *   offsets   [F+1] int64, device, non-decreasing, offsets[0] = 0
+ *   F         1 <= F <= 2^24
+ *   B         Metropolis steps (as pf_resample_metropolis, B >= 0 only)
+ *   seeds     [F] uint64, device: filter f uses key seeds[f] and filter id f
+ *   ancestors concatenated like logw; filter-local indices in [0, P_f)
+ * Each filter must have P_f <= 2^31 - 1; an empty filter is skipped.
+ * A filter with NaN/+inf or all -inf log-weights sets device status
+ * PF_ERR_DOMAIN (its ancestors are unspecified; other filters are unaffected).
+ */
+pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B,
+                              const uint64_t* seeds, int32_t* ancestors, void* stream);
+
+/*
+ * Pre-size the workspace of `stream` for single-filter calls with up to P_max
+ * particles and batched calls with up to total_max particles in up to F_max
+ * filters, so that later calls allocate nothing.  Synchronous.
+ */
+pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream);
+
+/*
+ * Synchronise `stream`, return in *out the first device-side error recorded
+ * by calls on it since the last read (PF_OK if none), and clear it.
+ */
+pf_status pf_get_device_status(void* stream, pf_status* out);
+
+/*
+ * Bound on the number of Metropolis steps (Section 2, Eqs. 1-5): the
+ * smallest B with lambda^B <= eps (alpha + beta) / max(alpha, beta), where
+ * beta = 1/P, alpha = (1 - w_max)/(P w_max) and lambda = 1 - alpha - beta;
+ * w_max is the largest normalised weight.  Returns -1 for invalid arguments
+ * (P < 1, w_max outside (0, 1], eps <= 0).  Host-only, pure.
+ */
+int64_t pf_metropolis_B(int64_t P, double w_max, double eps);
+
+/* Human-readable name of a status code (static storage). */
+const char* pf_status_string(pf_status status);
+
+/*
+ * Upper limit, in nanoseconds, on every device-side wait of later calls (the
+ * grid-wide gathers of the single-launch kernels and the batched work
+ * queue).  A wait that runs out records PF_ERR_TIMEOUT and ends the kernel
+ * without writing further outputs.  Default 1e9 (one second).
+ */
+pf_status pf_set_wait_limit_ns(uint64_t ns);
+
+/*
+ * Fault injection for tests of the timeout path (host-side switch, read at
+ * launch): when tile >= 0, the next single-launch systematic/stratified call
+ * has that tile skip publishing its partial sum, so every wait on it runs out
+ * and the call records PF_ERR_TIMEOUT.  The switch clears itself after one
+ * call.  tile < 0 disarms it.
+ */
+pf_status pf_debug_skip_publish(int64_t tile);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int pf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_H_ */

@@ -1,0 +1,350 @@
+// C ABI of libpf (declared in include/pf.h): argument checks, the per-stream
+// workspace, and the choice of launch for each entry point.  All arithmetic
+// happens in the kernels; nothing here touches particle data on the host.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+namespace pf {
+cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0, uint32_t key1,
+                              uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms, cudaStream_t s);
+cudaError_t prepare_metropolis();
+cudaError_t launch_gather(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* anc, int64_t P_dst,
+                          void* dst, uint32_t* ctl, int num_sms, cudaStream_t s);
+cudaError_t launch_reduce(const float* lw, int64_t P, void* rec, uint32_t* ctl, float* ess_out, double* log_sum_out,
+                          uint32_t* B_out, double eps, uint32_t B_cap, cudaStream_t s);
+int reduce_tiles(int64_t P);
+size_t reduce_record_bytes();
+}  // namespace pf
+
+using namespace pf;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kMaxPersistTiles = 1024;
+constexpr uint32_t kMetroBCap = 1u << 24;
+
+struct DeviceInfo {
+    bool ready = false;
+    int num_sms = 0;
+    int persist_per_sm[3] = {0, 0, 0};
+};
+
+struct Workspace {
+    uint32_t* ctl = nullptr;     // CTL_WORDS control words
+    uint64_t* slots = nullptr;   // 4 words per tile of the single-launch kernels
+    void* scratch = nullptr;     // per-call scratch (multinomial cumulative weights, reduction records)
+    size_t scratch_bytes = 0;
+};
+
+std::mutex g_mu;
+DeviceInfo g_dev[kMaxDevices];
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+uint64_t g_wait_ns = 1000000000ull;
+int64_t g_skip_tile = -1;
+
+pf_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return PF_OK;
+    if (std::getenv("PF_VERBOSE")) std::fprintf(stderr, "libpf: %s: %s\n", what, cudaGetErrorString(e));
+    return PF_ERR_CUDA;
+}
+
+pf_status device_info(int& dev, DeviceInfo*& info) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return PF_ERR_CUDA;
+    info = &g_dev[dev];
+    if (info->ready) return PF_OK;
+    e = cudaDeviceGetAttribute(&info->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    for (int k = 0; k < 3; ++k) info->persist_per_sm[k] = persistent_blocks_per_sm(k);
+    e = prepare_metropolis();
+    if (e != cudaSuccess) return cuda_fail(e, "prepare_metropolis");
+    info->ready = true;
+    return PF_OK;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Workspace of (current device, stream) with at least `scratch` bytes.  Caller holds g_mu.
+pf_status workspace(cudaStream_t s, size_t scratch, Workspace*& out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    Workspace& w = g_ws[{dev, s}];
+    if (!w.ctl) {
+        if (capturing(s)) return PF_ERR_NOMEM;
+        e = cudaMalloc(&w.ctl, CTL_WORDS * sizeof(uint32_t));
+        if (e != cudaSuccess) return PF_ERR_NOMEM;
+        e = cudaMalloc(&w.slots, 4 * kMaxPersistTiles * sizeof(uint64_t));
+        if (e != cudaSuccess) return PF_ERR_NOMEM;
+        e = cudaMemsetAsync(w.ctl, 0, CTL_WORDS * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.slots, 0, 4 * kMaxPersistTiles * sizeof(uint64_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    if (scratch > w.scratch_bytes) {
+        if (capturing(s)) return PF_ERR_NOMEM;
+        // the old scratch may still be in use by work queued on this stream
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        if (w.scratch) cudaFree(w.scratch);
+        w.scratch = nullptr;
+        w.scratch_bytes = 0;
+        size_t sz = scratch < 4096 ? 4096 : scratch;
+        e = cudaMalloc(&w.scratch, sz);
+        if (e != cudaSuccess) return PF_ERR_NOMEM;
+        w.scratch_bytes = sz;
+    }
+    out = &w;
+    return PF_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+size_t reduce_scratch(int64_t P) { return (size_t)reduce_tiles(P) * reduce_record_bytes(); }
+
+// Tile layout of a single-launch call: grid G <= G_max tiles of `tile` elements
+// (a multiple of 4), at least ~2K elements per tile.
+bool persistent_layout(int64_t P, int G_max, int& G, int& tile) {
+    if (G_max < 1) return false;
+    if (G_max > kMaxPersistTiles) G_max = kMaxPersistTiles;
+    if (P > (int64_t)G_max * kTileMax) return false;
+    const char* env = std::getenv("PF_MIN_TILE");
+    int64_t min_tile = env ? std::atoll(env) : 2048;
+    if (min_tile < 4) min_tile = 4;
+    int64_t g = (P + min_tile - 1) / min_tile;
+    if (g > G_max) g = G_max;
+    if (g < 1) g = 1;
+    int64_t t = (P + g - 1) / g;
+    t = (t + 3) & ~int64_t(3);
+    if (t > kTileMax) t = kTileMax;
+    g = (P + t - 1) / t;
+    G = (int)g;
+    tile = (int)t;
+    return G <= G_max;
+}
+
+pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t seed, int32_t* anc, void* stream) {
+    if (!logw || !anc || P < 1 || P > PF_MAX_PARTICLES) return PF_ERR_INVALID;
+    if (!aligned16(logw) || !aligned16(anc)) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    int G, tile;
+    if (!persistent_layout(P, info->num_sms * info->persist_per_sm[kind], G, tile)) {
+        return PF_ERR_INVALID;  // larger P: multi-pass path
+    }
+    Workspace* w;
+    st = workspace(s, kind == PF_MULTINOMIAL ? (size_t)P * sizeof(float) : 0, w);
+    if (st) return st;
+    SortedParams p;
+    p.lw = logw;
+    p.anc = anc;
+    p.P = P;
+    p.tile = tile;
+    p.n_tiles = G;
+    p.key0 = (uint32_t)(seed & 0xffffffffu);
+    p.key1 = (uint32_t)(seed >> 32);
+    p.filter = 0;
+    p.ctl = w->ctl;
+    p.slots = w->slots;
+    p.wait_ns = g_wait_ns;
+    p.skip_tile = (int)g_skip_tile;
+    g_skip_tile = -1;
+    p.v_out = kind == PF_MULTINOMIAL ? (float*)w->scratch : nullptr;
+    return cuda_fail(launch_sorted_persistent(kind, p, G, s), "persistent launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_resample_systematic(const float* logw, int64_t P, int B, uint64_t seed, int32_t* ancestors,
+                                 void* stream) {
+    (void)B;
+    return resample_cumulative(PF_SYSTEMATIC, logw, P, seed, ancestors, stream);
+}
+
+pf_status pf_resample_stratified(const float* logw, int64_t P, int B, uint64_t seed, int32_t* ancestors,
+                                 void* stream) {
+    (void)B;
+    return resample_cumulative(PF_STRATIFIED, logw, P, seed, ancestors, stream);
+}
+
+pf_status pf_resample_multinomial(const float* logw, int64_t P, int B, uint64_t seed, int32_t* ancestors,
+                                  void* stream) {
+    (void)B;
+    return resample_cumulative(PF_MULTINOMIAL, logw, P, seed, ancestors, stream);
+}
+
+pf_status pf_resample_metropolis(const float* logw, int64_t P, int B, uint64_t seed, int32_t* ancestors,
+                                 void* stream) {
+    if (!logw || !ancestors || P < 1 || P > PF_MAX_PARTICLES) return PF_ERR_INVALID;
+    if (!aligned16(logw) || !aligned16(ancestors)) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    Workspace* w;
+    st = workspace(s, B < 0 ? reduce_scratch(P) : 0, w);
+    if (st) return st;
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    const uint32_t* B_dev = nullptr;
+    if (B < 0) {
+        cudaError_t e = launch_reduce(logw, P, w->scratch, w->ctl, nullptr, nullptr, w->ctl + CTL_METRO_B, 0.01,
+                                      kMetroBCap, s);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+        B_dev = w->ctl + CTL_METRO_B;
+    }
+    return cuda_fail(launch_metropolis(logw, P, B, B_dev, k0, k1, 0u, ancestors, w->ctl, info->num_sms, s),
+                     "metropolis launch");
+}
+
+pf_status pf_gather(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* ancestors, int64_t P_dst,
+                    void* dst, void* stream) {
+    if (!src || !dst || !ancestors || P_src < 1 || P_dst < 0 || row_bytes <= 0 || (row_bytes & 3)) {
+        return PF_ERR_INVALID;
+    }
+    if (P_dst == 0) return PF_OK;
+    const uintptr_t s0 = (uintptr_t)src, s1 = s0 + (uintptr_t)(P_src * row_bytes);
+    const uintptr_t d0 = (uintptr_t)dst, d1 = d0 + (uintptr_t)(P_dst * row_bytes);
+    if (s0 < d1 && d0 < s1) return PF_ERR_INVALID;  // overlapping src and dst
+    if (((uintptr_t)src & 3) || ((uintptr_t)dst & 3) || ((uintptr_t)ancestors & 3)) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    Workspace* w;
+    st = workspace(s, 0, w);
+    if (st) return st;
+    return cuda_fail(launch_gather(src, P_src, row_bytes, ancestors, P_dst, dst, w->ctl, info->num_sms, s),
+                     "gather launch");
+}
+
+pf_status pf_ess(const float* logw, int64_t P, float* ess_out, double* log_sum_out, void* stream) {
+    if (!logw || !ess_out || P < 1 || P > PF_MAX_PARTICLES || !aligned16(logw)) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    Workspace* w;
+    st = workspace(s, reduce_scratch(P), w);
+    if (st) return st;
+    return cuda_fail(launch_reduce(logw, P, w->scratch, w->ctl, ess_out, log_sum_out, nullptr, 0.0, 0u, s),
+                     "reduce launch");
+}
+
+pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B,
+                              const uint64_t* seeds, int32_t* ancestors, void* stream) {
+    (void)kind;
+    (void)logw;
+    (void)offsets;
+    (void)F;
+    (void)B;
+    (void)seeds;
+    (void)ancestors;
+    (void)stream;
+    return PF_ERR_INVALID;
+}
+
+pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) {
+    if (P_max < 0 || total_max < 0 || F_max < 0) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    size_t need = (size_t)P_max * sizeof(float);
+    const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
+    if (red > need) need = red;
+    Workspace* w;
+    st = workspace(s, need, w);
+    if (st) return st;
+    return cuda_fail(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+}
+
+pf_status pf_get_device_status(void* stream, pf_status* out) {
+    if (!out) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    auto it = g_ws.find({dev, s});
+    if (it == g_ws.end() || !it->second.ctl) {
+        e = cudaStreamSynchronize(s);
+        *out = PF_OK;
+        return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    uint32_t v = 0;
+    e = cudaMemcpyAsync(&v, it->second.ctl + CTL_STATUS, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(it->second.ctl + CTL_STATUS, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    *out = (pf_status)v;
+    return PF_OK;
+}
+
+int64_t pf_metropolis_B(int64_t P, double w_max, double eps) {
+    if (P < 1 || !(w_max > 0.0) || w_max > 1.0 || !(eps > 0.0)) return -1;
+    const double beta = 1.0 / (double)P;
+    const double alpha = (1.0 - w_max) / ((double)P * w_max);
+    const double lambda = 1.0 - alpha - beta;
+    const double target = eps * (alpha + beta) / (alpha > beta ? alpha : beta);
+    if (target >= 1.0) return 0;
+    if (lambda <= 0.0) return 1;
+    double b = std::ceil(std::log(target) / std::log(lambda));
+    if (b >= 1.0 && std::pow(lambda, b - 1.0) <= target) b -= 1.0;
+    return (int64_t)b;
+}
+
+const char* pf_status_string(pf_status status) {
+    switch (status) {
+    case PF_OK: return "ok";
+    case PF_ERR_INVALID: return "invalid argument";
+    case PF_ERR_DOMAIN: return "domain error (NaN/+inf log-weight or all weights zero)";
+    case PF_ERR_TIMEOUT: return "device-side wait ran out";
+    case PF_ERR_CUDA: return "CUDA error";
+    case PF_ERR_NOMEM: return "workspace allocation failed or needed during capture";
+    }
+    return "unknown status";
+}
+
+pf_status pf_set_wait_limit_ns(uint64_t ns) {
+    if (ns == 0) return PF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_wait_ns = ns;
+    return PF_OK;
+}
+
+pf_status pf_debug_skip_publish(int64_t tile) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_skip_tile = tile < 0 ? -1 : tile;
+    return PF_OK;
+}
+
+int pf_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,222 @@
+// Device-side building blocks shared by the resampling kernels.
+//
+// Everything here is written for sm_103a (GB300): 32-wide warps, FP32 per
+// element, FP64 only for per-tile carries (FP64 issue rate on this part is a
+// small fraction of FP32), integer Philox.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pf_internal.h"
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// whose halves are permuted and xored with the other counter words and the
+// round key; the key advances by the Weyl increments each round.
+// ---------------------------------------------------------------------------
+struct u32x4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a_lo = 0xD2511F53u * c0;
+        const uint32_t a_hi = __umulhi(0xD2511F53u, c0);
+        const uint32_t b_lo = 0xCD9E8D57u * c2;
+        const uint32_t b_hi = __umulhi(0xCD9E8D57u, c2);
+        c0 = b_hi ^ c1 ^ k0;
+        c1 = b_lo;
+        c2 = a_hi ^ c3 ^ k1;
+        c3 = a_lo;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return {c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t word_of(const u32x4& r, int s) {
+    return s == 0 ? r.x : (s == 1 ? r.y : (s == 2 ? r.z : r.w));
+}
+
+// u23: odd multiples of 2^-24 in (0,1); exact in float.
+__device__ __forceinline__ float u23f(uint32_t x) {
+    return __uint2float_rn(((x >> 9) << 1) | 1u) * 0x1p-24f;
+}
+
+// u32 = (2x+1) 2^-33 as an exact float pair (hi carries the top 24 bits).
+__device__ __forceinline__ void u32_pair(uint32_t x, float& hi, float& lo) {
+    hi = __uint2float_rn(x >> 8) * 0x1p-24f;
+    lo = __uint2float_rn(((x & 0xFFu) << 1) | 1u) * 0x1p-33f;
+}
+
+__device__ __forceinline__ uint32_t draw_index(uint32_t x, uint32_t P) { return __umulhi(x, P); }
+
+// ---------------------------------------------------------------------------
+// Error-free transformations (Knuth's TwoSum) and float pairs.  The __f*_rn
+// intrinsics keep the compiler from contracting or reordering them.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct fpair {
+    float hi, lo;
+};
+
+__device__ __forceinline__ fpair pair_add(fpair a, fpair b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, e);
+    const float lo = __fsub_rn(e, __fsub_rn(hi, s));
+    return {hi, lo};
+}
+
+// ---------------------------------------------------------------------------
+// Tile reference.  A tile's weights are taken relative to 2^k (k near the
+// tile's largest log-weight times log2 e), i.e. w_i = exp(lw_i - k ln 2).
+// The reference k ln 2 is held as a float pair so that lw_i - k ln 2 is
+// formed without rounding loss, and tiles with different k combine by exact
+// binary scaling.
+// ---------------------------------------------------------------------------
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr float kLn2Hi = (float)kLn2;
+constexpr float kLn2Lo = (float)(kLn2 - (double)(float)kLn2);
+constexpr float kLog2e = 1.44269504088896340736f;
+
+__device__ __forceinline__ int tile_exponent(float m) {
+    // m = -inf (every weight zero in the tile): any k works, take 0.
+    if (!(m > -INFINITY)) return 0;
+    float km = fminf(fmaxf(m * kLog2e, -1.0e9f), 1.0e9f);
+    return (int)ceilf(km);
+}
+
+__device__ __forceinline__ fpair tile_reference(int k) {
+    const float kf = (float)k;  // |k| <= 1e9: exact enough; k below 2^24 is exact
+    const float hi = __fmul_rn(kf, kLn2Hi);
+    const float err = __fmaf_rn(kf, kLn2Hi, -hi);
+    return {hi, __fmaf_rn(kf, kLn2Lo, err)};
+}
+
+// exp(lw - R) with R = (R.hi, R.lo): the subtraction is error-free, the
+// residual enters as a first-order factor.  Zero for lw = -inf.
+__device__ __forceinline__ float weight_rel(float lw, fpair R) {
+    float s, e;
+    two_sum(lw, -R.hi, s, e);
+    const float d_lo = __fsub_rn(e, R.lo);
+    const float x = expf(s);
+    return x > 0.f ? __fmaf_rn(x, d_lo, x) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// Status word and bounded waits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t code) {
+    atomicCAS(status, 0u, code);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t tag_slot(uint32_t epoch, uint32_t bits) {
+    return ((uint64_t)epoch << 32) | bits;
+}
+
+// Spin (bounded) until *p carries epoch in its high word; returns false on timeout.
+__device__ __forceinline__ bool wait_slot(const uint64_t* p, uint32_t epoch, uint64_t t_start,
+                                          uint64_t limit_ns, uint32_t& bits) {
+    for (uint32_t it = 0;; ++it) {
+        const uint64_t v = ld_acquire_u64(p);
+        if ((uint32_t)(v >> 32) == epoch) {
+            bits = (uint32_t)v;
+            return true;
+        }
+        if ((it & 63u) == 63u) {
+            if (global_ns() - t_start > limit_ns) return false;
+            __nanosleep(64);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp and block collectives.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int warp_max_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Inclusive warp scan of float pairs.
+__device__ __forceinline__ fpair warp_scan_pair(fpair v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float h = __shfl_up_sync(0xffffffffu, v.hi, o);
+        const float l = __shfl_up_sync(0xffffffffu, v.lo, o);
+        if (lane >= o) v = pair_add({h, l}, v);
+    }
+    return v;
+}
+
+__device__ __forceinline__ float warp_scan_max(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float h = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v = fmaxf(v, h);
+    }
+    return v;
+}
+
+// Inclusive warp scan of doubles (carries only).
+__device__ __forceinline__ double warp_scan_d(double v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double h = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += h;
+    }
+    return v;
+}
+
+}  // namespace pf

@@ -1,0 +1,64 @@
+// Internal declarations shared by the host API and the kernels of libpf.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pf {
+
+// Status codes (mirror pf_status in include/pf.h).
+enum : uint32_t {
+    ST_OK = 0,
+    ST_INVALID = 1,
+    ST_DOMAIN = 2,
+    ST_TIMEOUT = 3,
+};
+
+// Philox stream tags (counter word 3).
+enum : uint32_t { TAG_SYS = 1, TAG_STRAT = 2, TAG_MULTI = 3, TAG_METRO = 4 };
+
+// Control words kept in the per-stream workspace.
+enum : int {
+    CTL_STATUS = 0,       // first device-side error (pf_status code)
+    CTL_EPOCH = 1,        // launch epoch of the single-launch kernels
+    CTL_ESS_COUNT = 2,    // arrival counter of the ESS reduction
+    CTL_TILE_TICKET = 3,  // tile ticket of the lookback scan
+    CTL_QUEUE = 4,        // work-queue ticket of the batched kernels
+    CTL_QUEUE_DONE = 5,   // completion counter of the batched kernels
+    CTL_METRO_B = 6,      // Metropolis step count chosen on the device
+    CTL_WORDS = 16
+};
+
+constexpr int kThreads = 512;     // threads per CTA of the tile kernels
+constexpr int kMaxPerThread = 16; // elements per thread (multiple of 4)
+constexpr int kTileMax = kThreads * kMaxPerThread;
+
+// Per-tile record of the multi-pass scan (decoupled lookback).
+struct TileRecord {
+    int32_t k;        // tile exponent: weights are relative to 2^k
+    int32_t i_last;   // last positive-weight element of the tile (tile-local), -1 if none
+    float s_hi, s_lo; // tile sum (compensated pair), relative to 2^k
+    double excl;      // exclusive prefix of the tile, relative to 2^excl_k
+    int32_t excl_k;
+    uint32_t flags;   // bit 0: aggregate ready, bit 1: inclusive ready (per epoch, see kernels)
+};
+
+struct SortedParams {
+    const float* lw;
+    int32_t* anc;
+    int64_t P;
+    int tile;      // elements per tile (multiple of 4, <= kTileMax)
+    int n_tiles;   // tiles (CTAs) of the launch
+    uint32_t key0, key1, filter;
+    uint32_t* ctl;
+    uint64_t* slots;  // 3 words per tile
+    uint64_t wait_ns;
+    int skip_tile;
+    float* v_out;     // multinomial: tile-local cumulative weights (P floats), else null
+};
+
+// Kernel launchers (defined in the .cu files; return the launch error).
+cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s);
+int persistent_blocks_per_sm(int kind);
+
+}  // namespace pf

@@ -1,0 +1,96 @@
+// Metropolis resampler (Figure 1d, Section 2).
+//
+// Thread i runs chain i: k = i, then B steps, each proposing j uniformly over
+// all P indices and moving to it when lw_j >= lw_k or when u < exp(lw_j - lw_k).
+// No sum of weights is formed, so there is no collective step and one launch
+// suffices.  Each Philox-4x32-10 call supplies the (proposal, uniform) pairs of
+// two consecutive steps.  The log-weights are read either from shared memory
+// (a CTA-wide copy, when P floats fit) or through L2 (ld.global.nc), where a
+// 4 MiB vector of P = 2^20 log-weights stays resident.
+#include "pf_device.cuh"
+
+namespace pf {
+
+constexpr int kMetroThreads = 256;
+constexpr int kMetroSmemFloats = 48 * 1024;  // 192 KiB staging limit
+
+// Accept a move from k to j (log-weights lk, lj) with uniform u.
+__device__ __forceinline__ bool metropolis_accept(float lj, float lk, float u) {
+    if (lj >= lk) return true;  // also covers lk = -inf
+    float s, e;
+    two_sum(lj, -lk, s, e);
+    const float x = expf(s);
+    const float r = x > 0.f ? __fmaf_rn(x, e, x) : 0.f;
+    return u < r;
+}
+
+template <bool STAGED>
+__global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __restrict__ lw, int64_t P, int B,
+                                                              const uint32_t* __restrict__ B_dev, uint32_t key0,
+                                                              uint32_t key1, uint32_t filter,
+                                                              int32_t* __restrict__ anc, uint32_t* ctl) {
+    extern __shared__ float wsm[];
+    if (STAGED) {
+        // the whole log-weight vector, 16-byte copies (lw is 16-byte aligned)
+        const int n4 = (int)(P >> 2);
+        for (int q = threadIdx.x; q < n4; q += blockDim.x)
+            reinterpret_cast<float4*>(wsm)[q] = __ldg(reinterpret_cast<const float4*>(lw) + q);
+        for (int q = 4 * n4 + threadIdx.x; q < P; q += blockDim.x) wsm[q] = __ldg(lw + q);
+        __syncthreads();
+    }
+    const int steps = B_dev ? (int)__ldg(B_dev) : B;
+    const uint32_t Pu = (uint32_t)P;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        float lk = STAGED ? wsm[i] : __ldg(lw + i);
+        if (!(lk <= 3.402823466e38f)) set_status(ctl + CTL_STATUS, ST_DOMAIN);  // NaN or +inf
+        uint32_t k = (uint32_t)i;
+        for (int b = 0; b < steps; b += 2) {
+            const u32x4 r = philox((uint32_t)i, (uint32_t)(b >> 1), filter, TAG_METRO, key0, key1);
+            {
+                const uint32_t j = draw_index(r.x, Pu);
+                const float lj = STAGED ? wsm[j] : __ldg(lw + j);
+                if (metropolis_accept(lj, lk, u23f(r.y))) {
+                    k = j;
+                    lk = lj;
+                }
+            }
+            if (b + 1 < steps) {
+                const uint32_t j = draw_index(r.z, Pu);
+                const float lj = STAGED ? wsm[j] : __ldg(lw + j);
+                if (metropolis_accept(lj, lk, u23f(r.w))) {
+                    k = j;
+                    lk = lj;
+                }
+            }
+        }
+        anc[i] = (int32_t)k;
+    }
+}
+
+// Once per device: allow the staged variant its full shared-memory copy.
+cudaError_t prepare_metropolis() {
+    return cudaFuncSetAttribute(k_metropolis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMetroSmemFloats * (int)sizeof(float));
+}
+
+cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0, uint32_t key1,
+                              uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms, cudaStream_t s) {
+    const bool staged = P <= kMetroSmemFloats;
+    const int64_t blocks_needed = (P + kMetroThreads - 1) / kMetroThreads;
+    if (staged) {
+        // every CTA stages the full vector, so keep the grid to what runs at once
+        const size_t smem = (size_t)P * sizeof(float);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_metropolis<true>, kMetroThreads, smem);
+        if (per_sm < 1) per_sm = 1;
+        const int64_t grid = blocks_needed < (int64_t)num_sms * per_sm ? blocks_needed : (int64_t)num_sms * per_sm;
+        k_metropolis<true><<<(unsigned)grid, kMetroThreads, smem, s>>>(lw, P, B, B_dev, key0, key1, filter, anc, ctl);
+    } else {
+        const int64_t cap = (int64_t)num_sms * 64;
+        const int64_t grid = blocks_needed < cap ? blocks_needed : cap;
+        k_metropolis<false><<<(unsigned)grid, kMetroThreads, 0, s>>>(lw, P, B, B_dev, key0, key1, filter, anc, ctl);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -1,0 +1,254 @@
+// Ancestor gather (Section 1, step 4) and the weight reduction behind the
+// effective sample size (Section 3) and the device-side choice of the
+// Metropolis step count (Section 2, Eqs. 1-5).
+#include <climits>
+
+#include "pf_device.cuh"
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// Gather: dst row j <- src row anc[j].  One thread moves one VT-sized chunk;
+// each thread handles kUnroll chunks spread a grid apart, issuing all loads
+// before the stores so that several random row reads are in flight.
+// ---------------------------------------------------------------------------
+constexpr int kGatherThreads = 256;
+constexpr int kUnroll = 4;
+
+template <typename VT, bool POW2>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(const VT* __restrict__ src, int64_t P_src, int64_t vecs,
+                                                           int vshift, const int32_t* __restrict__ anc,
+                                                           int64_t P_dst, VT* __restrict__ dst, uint32_t* ctl) {
+    const int64_t total = P_dst * vecs;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < total; base += stride * kUnroll) {
+        VT v[kUnroll];
+        int64_t idx[kUnroll];
+        bool ok[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            idx[u] = base + u * stride;
+            ok[u] = false;
+            if (idx[u] < total) {
+                const int64_t j = POW2 ? (idx[u] >> vshift) : idx[u] / vecs;
+                const int64_t c = POW2 ? (idx[u] & (vecs - 1)) : idx[u] - j * vecs;
+                const int32_t a = __ldg(anc + j);
+                if (a >= 0 && a < P_src) {
+                    v[u] = __ldg(src + (int64_t)a * vecs + c);
+                    ok[u] = true;
+                } else if (c == 0) {
+                    set_status(ctl + CTL_STATUS, ST_INVALID);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (ok[u]) __stcs(dst + idx[u], v[u]);
+    }
+}
+
+template <typename VT>
+static cudaError_t gather_vt(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* anc, int64_t P_dst,
+                             void* dst, uint32_t* ctl, int num_sms, cudaStream_t s) {
+    const int64_t vecs = row_bytes / (int64_t)sizeof(VT);
+    const int64_t total = P_dst * vecs;
+    int64_t blocks = (total + (int64_t)kGatherThreads * kUnroll - 1) / ((int64_t)kGatherThreads * kUnroll);
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    const bool pow2 = (vecs & (vecs - 1)) == 0;
+    int vshift = 0;
+    while (pow2 && (1LL << vshift) < vecs) ++vshift;
+    if (pow2)
+        k_gather<VT, true><<<(unsigned)blocks, kGatherThreads, 0, s>>>(
+            (const VT*)src, P_src, vecs, vshift, anc, P_dst, (VT*)dst, ctl);
+    else
+        k_gather<VT, false><<<(unsigned)blocks, kGatherThreads, 0, s>>>(
+            (const VT*)src, P_src, vecs, vshift, anc, P_dst, (VT*)dst, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* anc, int64_t P_dst,
+                          void* dst, uint32_t* ctl, int num_sms, cudaStream_t s) {
+    const uintptr_t a = (uintptr_t)src | (uintptr_t)dst | (uintptr_t)row_bytes;
+    if ((a & 15) == 0) return gather_vt<uint4>(src, P_src, row_bytes, anc, P_dst, dst, ctl, num_sms, s);
+    if ((a & 7) == 0) return gather_vt<uint2>(src, P_src, row_bytes, anc, P_dst, dst, ctl, num_sms, s);
+    return gather_vt<uint32_t>(src, P_src, row_bytes, anc, P_dst, dst, ctl, num_sms, s);
+}
+
+// ---------------------------------------------------------------------------
+// Weight reduction: per tile (k_t, sum w, sum w^2, max lw) with weights taken
+// relative to 2^k_t; the last CTA to finish combines the tiles in index order
+// in FP64 and writes ESS = (sum w)^2 / sum w^2, log sum exp(lw), and, when
+// asked, the Metropolis step bound of Eq. 5 for the actual w_max.
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedPerThread = 16;
+constexpr int kRedTile = kRedThreads * kRedPerThread;
+
+struct RedRecord {
+    int32_t k;
+    float m;
+    float s_hi, s_lo, q_hi, q_lo;
+    uint32_t bad, pad;
+};
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float w) {
+    const float y = __fsub_rn(w, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+__device__ __forceinline__ double metropolis_bound(double P, double w_max, double eps) {
+    const double beta = 1.0 / P;
+    const double alpha = (1.0 - w_max) / (P * w_max);
+    const double lambda = 1.0 - alpha - beta;
+    const double target = eps * (alpha + beta) / fmax(alpha, beta);
+    if (target >= 1.0) return 0.0;
+    if (lambda <= 0.0) return 1.0;
+    return ceil(log(target) / log(lambda));
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict__ lw, int64_t P, RedRecord* rec,
+                                                        uint32_t* ctl, float* ess_out, double* log_sum_out,
+                                                        uint32_t* B_out, double eps, uint32_t B_cap) {
+    __shared__ float rm[kRedThreads / 32];
+    __shared__ fpair rs[kRedThreads / 32], rq[kRedThreads / 32];
+    __shared__ int last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * kRedTile;
+    const int n = (int)min((int64_t)kRedTile, P - t0);
+    const float* base = lw + t0;
+
+    float x[kRedPerThread];
+#pragma unroll
+    for (int q = 0; q < kRedPerThread / 4; ++q) {
+        // coalesced: thread tid reads vector q*kRedThreads + tid
+        const int e = 4 * (q * kRedThreads + tid);
+        if (e + 3 < n) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(base + e));
+            x[4 * q] = v.x;
+            x[4 * q + 1] = v.y;
+            x[4 * q + 2] = v.z;
+            x[4 * q + 3] = v.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) x[4 * q + r] = (e + r < n) ? __ldg(base + e + r) : -INFINITY;
+        }
+    }
+    float m = -INFINITY;
+    int bad = 0;
+#pragma unroll
+    for (int i = 0; i < kRedPerThread; ++i) {
+        bad |= !(x[i] <= 3.402823466e38f);
+        m = fmaxf(m, x[i]);
+    }
+    m = warp_max(m);
+    if (lane == 0) rm[warp] = m;
+    bad = __syncthreads_or(bad);
+    float mt = rm[0];
+#pragma unroll
+    for (int w = 1; w < kRedThreads / 32; ++w) mt = fmaxf(mt, rm[w]);
+    const int k = tile_exponent(mt);
+    const fpair R = tile_reference(k);
+    float s = 0.f, sc = 0.f, q = 0.f, qc = 0.f;
+#pragma unroll
+    for (int i = 0; i < kRedPerThread; ++i) {
+        const float w = weight_rel(x[i], R);
+        kahan_add(s, sc, w);
+        kahan_add(q, qc, w * w);
+    }
+    fpair ps = {s, -sc}, pq = {q, -qc};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ps = pair_add(ps, {__shfl_xor_sync(0xffffffffu, ps.hi, o), __shfl_xor_sync(0xffffffffu, ps.lo, o)});
+        pq = pair_add(pq, {__shfl_xor_sync(0xffffffffu, pq.hi, o), __shfl_xor_sync(0xffffffffu, pq.lo, o)});
+    }
+    if (lane == 0) {
+        rs[warp] = ps;
+        rq[warp] = pq;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        fpair S = rs[0], Q = rq[0];
+        for (int w = 1; w < kRedThreads / 32; ++w) {
+            S = pair_add(S, rs[w]);
+            Q = pair_add(Q, rq[w]);
+        }
+        RedRecord r;
+        r.k = k;
+        r.m = mt;
+        r.s_hi = S.hi;
+        r.s_lo = S.lo;
+        r.q_hi = Q.hi;
+        r.q_lo = Q.lo;
+        r.bad = bad;
+        r.pad = 0;
+        rec[blockIdx.x] = r;
+        __threadfence();
+        const uint32_t prev = atomicAdd(ctl + CTL_ESS_COUNT, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // last CTA: combine the tiles in index order (FP64)
+    if (tid < 32) {
+        const int T = gridDim.x;
+        int kmax = INT_MIN, anybad = 0;
+        float mmax = -INFINITY;
+        for (int t = lane; t < T; t += 32) {
+            anybad |= (int)__ldcg(&rec[t].bad);
+            if (__ldcg(&rec[t].s_hi) > 0.f) kmax = max(kmax, __ldcg(&rec[t].k));
+            mmax = fmaxf(mmax, __ldcg(&rec[t].m));
+        }
+        kmax = warp_max_i(kmax);
+        anybad = __any_sync(0xffffffffu, anybad);
+        mmax = warp_max(mmax);
+        double S = 0.0, Q = 0.0;
+        if (!anybad && kmax != INT_MIN) {
+            for (int t = lane; t < T; t += 32) {
+                const int kk = __ldcg(&rec[t].k) - kmax;
+                S += ldexp((double)__ldcg(&rec[t].s_hi) + (double)__ldcg(&rec[t].s_lo), kk);
+                Q += ldexp((double)__ldcg(&rec[t].q_hi) + (double)__ldcg(&rec[t].q_lo), 2 * kk);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                S += __shfl_xor_sync(0xffffffffu, S, o);
+                Q += __shfl_xor_sync(0xffffffffu, Q, o);
+            }
+        }
+        if (lane == 0) {
+            if (anybad || kmax == INT_MIN) {
+                set_status(ctl + CTL_STATUS, ST_DOMAIN);
+                if (ess_out) *ess_out = NAN;
+                if (log_sum_out) *log_sum_out = NAN;
+                if (B_out) *B_out = 0;
+            } else {
+                const double log_sum = (double)kmax * kLn2 + log(S);
+                if (ess_out) *ess_out = (float)(S * S / Q);
+                if (log_sum_out) *log_sum_out = log_sum;
+                if (B_out) {
+                    const double w_max = fmin(1.0, exp((double)mmax - log_sum));
+                    double b = metropolis_bound((double)P, w_max, eps);
+                    if (!(b >= 0.0)) b = (double)B_cap;
+                    *B_out = (uint32_t)fmin(b, (double)B_cap);
+                }
+            }
+            ctl[CTL_ESS_COUNT] = 0;  // ready for the next reduction on this stream
+        }
+    }
+}
+
+int reduce_tiles(int64_t P) { return (int)((P + kRedTile - 1) / kRedTile); }
+size_t reduce_record_bytes() { return sizeof(RedRecord); }
+
+cudaError_t launch_reduce(const float* lw, int64_t P, void* rec, uint32_t* ctl, float* ess_out, double* log_sum_out,
+                          uint32_t* B_out, double eps, uint32_t B_cap, cudaStream_t s) {
+    k_reduce<<<reduce_tiles(P), kRedThreads, 0, s>>>(lw, P, (RedRecord*)rec, ctl, ess_out, log_sum_out, B_out, eps,
+                                                     B_cap);
+    return cudaGetLastError();
+}
+
+}  // namespace pf

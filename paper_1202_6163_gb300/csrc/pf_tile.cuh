@@ -1,0 +1,189 @@
+// Tile scan: the per-tile half of the collective prefix sum of weights
+// (Section 2: multinomial, stratified and systematic resamplers need the
+// cumulative weights c_i).
+//
+// One CTA of kThreads threads owns a tile of n <= kTileMax consecutive
+// log-weights.  Thread k holds K consecutive elements (K in {4, 8, 16}) in
+// registers, loaded with 128-bit accesses.  The tile:
+//   1. finds its largest log-weight m_t and exponent k_t ~ m_t log2 e;
+//   2. forms w_i = exp(lw_i - k_t ln 2) with an error-free subtraction;
+//   3. runs a Kahan-compensated serial scan per thread and a block scan of the
+//      per-thread totals in float pairs;
+//   4. writes the tile-local inclusive cumulative weights v_i (float, made
+//      monotone across threads) to shared memory.  The sign bit of v_i marks
+//      zero-weight elements, which the searches never return.
+#pragma once
+
+#include "pf_device.cuh"
+
+namespace pf {
+
+constexpr int kWarps = kThreads / 32;
+
+struct TileShared {
+    float vs[kTileMax];        // v_i, sign bit set for zero weights
+    float Vb[kThreads + 1];    // per-thread bases, monotone
+    float redf[kWarps];
+    fpair redp[kWarps];
+    fpair total;
+    int i_last;
+};
+
+struct TileSummary {
+    int k;        // tile exponent
+    fpair S;      // tile sum relative to 2^k (compensated pair)
+    int i_last;   // tile-local index of the last positive weight, -1 if none
+    int bad;      // a NaN or +inf log-weight was seen
+};
+
+__device__ __forceinline__ int per_thread_count(int n) {
+    const int q = (n + kThreads - 1) / kThreads;
+    return q <= 4 ? 4 : (q <= 8 ? 8 : 16);
+}
+
+__device__ __forceinline__ bool zero_flag(float v) { return __float_as_uint(v) >> 31; }
+
+// Loads this thread's K elements (tile-local e0 .. e0+K) of base[0..n); base is
+// 16-byte aligned.  Out-of-range slots read as -inf.
+__device__ __forceinline__ void tile_load(const float* __restrict__ base, int n, int e0, int K,
+                                          float (&x)[kMaxPerThread]) {
+#pragma unroll
+    for (int q = 0; q < kMaxPerThread / 4; ++q) {
+        const int idx = e0 + 4 * q;
+        if (4 * q < K && idx + 3 < n) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(base + idx));
+            x[4 * q + 0] = v.x;
+            x[4 * q + 1] = v.y;
+            x[4 * q + 2] = v.z;
+            x[4 * q + 3] = v.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                x[4 * q + r] = (4 * q < K && idx + r < n) ? __ldg(base + idx + r) : -INFINITY;
+        }
+    }
+}
+
+// Block-wide; every thread of the CTA must call it.  Leaves sm.vs[0..n) filled
+// and returns the tile summary (identical in every thread).
+__device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base, int n, TileShared& sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = per_thread_count(n);
+    const int e0 = tid * K;
+
+    if (tid == 0) sm.i_last = -1;
+
+    float x[kMaxPerThread];
+    tile_load(base, n, e0, K, x);
+
+    // 1. tile maximum and domain check
+    float m = -INFINITY;
+    int bad = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxPerThread; ++i) {
+        bad |= !(x[i] <= 3.402823466e38f);  // NaN or +inf
+        m = fmaxf(m, x[i]);
+    }
+    m = warp_max(m);
+    if (lane == 0) sm.redf[warp] = m;
+    bad = __syncthreads_or(bad);
+    float mt = sm.redf[0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) mt = fmaxf(mt, sm.redf[w]);
+    const int k = tile_exponent(mt);
+    const fpair R = tile_reference(k);
+
+    // 2-3. weights and the compensated per-thread scan (x[] becomes the running sum)
+    float s = 0.f, c = 0.f;
+    int p = -1;
+    uint32_t posbits = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxPerThread; ++i) {
+        if (i < K) {
+            const float w = weight_rel(x[i], R);
+            if (w > 0.f) {
+                p = i;
+                posbits |= 1u << i;
+            }
+            const float y = __fsub_rn(w, c);
+            const float t = __fadd_rn(s, y);
+            c = __fsub_rn(__fsub_rn(t, s), y);
+            s = t;
+            x[i] = s;
+        }
+    }
+
+    // block exclusive scan of the per-thread totals (float pairs)
+    const fpair tot = {s, -c};
+    const fpair inc = warp_scan_pair(tot, lane);
+    fpair ex;
+    ex.hi = __shfl_up_sync(0xffffffffu, inc.hi, 1);
+    ex.lo = __shfl_up_sync(0xffffffffu, inc.lo, 1);
+    if (lane == 0) ex = {0.f, 0.f};
+    if (lane == 31) sm.redp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const fpair wv = lane < kWarps ? sm.redp[lane] : fpair{0.f, 0.f};
+        const fpair wi = warp_scan_pair(wv, lane);
+        fpair we;
+        we.hi = __shfl_up_sync(0xffffffffu, wi.hi, 1);
+        we.lo = __shfl_up_sync(0xffffffffu, wi.lo, 1);
+        if (lane == 0) we = {0.f, 0.f};
+        if (lane < kWarps) sm.redp[lane] = we;
+        if (lane == kWarps - 1) sm.total = wi;
+    }
+    __syncthreads();
+    const fpair E = pair_add(sm.redp[warp], ex);
+
+    // thread bases, made monotone by a running maximum
+    float V = __fadd_rn(E.hi, E.lo);
+    V = warp_scan_max(V, lane);
+    if (lane == 31) sm.redf[warp] = V;
+    if (p >= 0) atomicMax(&sm.i_last, e0 + p);
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) V = fmaxf(V, sm.redf[w]);
+    sm.Vb[tid] = V;
+    const fpair S = sm.total;
+    if (tid == kThreads - 1) sm.Vb[kThreads] = fmaxf(V, __fadd_rn(S.hi, S.lo));
+    __syncthreads();
+
+    // 4. tile-local cumulative weights; elements from the last positive one on
+    // take the next base so that no gap is left between threads
+    const float Vk = sm.Vb[tid], Vn = sm.Vb[tid + 1];
+#pragma unroll
+    for (int q = 0; q < kMaxPerThread / 4; ++q) {
+        if (4 * q < K && e0 + 4 * q < n) {
+            float o[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = 4 * q + r;
+                float v = (i >= p) ? Vn : fminf(__fadd_rn(Vk, x[i]), Vn);
+                o[r] = ((posbits >> i) & 1u) ? v : -v;
+            }
+            if (e0 + 4 * q + 3 < n) {
+                *reinterpret_cast<float4*>(&sm.vs[e0 + 4 * q]) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (e0 + 4 * q + r < n) sm.vs[e0 + 4 * q + r] = o[r];
+            }
+        }
+    }
+    __syncthreads();
+
+    TileSummary ts;
+    ts.k = k;
+    ts.S = S;
+    ts.i_last = sm.i_last;
+    ts.bad = bad;
+    return ts;
+}
+
+// First non-zero-weight element at or after i in vs[0..n); falls back to i_last.
+__device__ __forceinline__ int next_positive(const float* vs, int n, int i, int i_last) {
+    for (int q = i; q < n; ++q)
+        if (!zero_flag(vs[q])) return q;
+    return i_last;
+}
+
+}  // namespace pf

@@ -1,0 +1,159 @@
+"""Thin ctypes binding of libpf.so (declared in include/pf.h).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name.  Array arguments may be torch CUDA tensors (their data pointers are
+passed) or raw integer device addresses.  ``stream`` defaults to torch's
+current CUDA stream.  A non-zero status raises :class:`PFError`.  The library
+must have been built (``python -m paper_1202_6163_gb300.build``); there is no
+fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpf.so")
+
+PF_OK, PF_ERR_INVALID, PF_ERR_DOMAIN, PF_ERR_TIMEOUT, PF_ERR_CUDA, PF_ERR_NOMEM = range(6)
+PF_MULTINOMIAL, PF_STRATIFIED, PF_SYSTEMATIC, PF_METROPOLIS = range(4)
+STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_INVALID", 2: "PF_ERR_DOMAIN", 3: "PF_ERR_TIMEOUT", 4: "PF_ERR_CUDA",
+                5: "PF_ERR_NOMEM"}
+
+# name -> (restype, argtypes); the full set of symbols include/pf.h declares
+_VP, _I64, _U64, _INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+SIGNATURES = {
+    "pf_resample_systematic": (_INT, [_VP, _I64, _INT, _U64, _VP, _VP]),
+    "pf_resample_stratified": (_INT, [_VP, _I64, _INT, _U64, _VP, _VP]),
+    "pf_resample_multinomial": (_INT, [_VP, _I64, _INT, _U64, _VP, _VP]),
+    "pf_resample_metropolis": (_INT, [_VP, _I64, _INT, _U64, _VP, _VP]),
+    "pf_gather": (_INT, [_VP, _I64, _I64, _VP, _I64, _VP, _VP]),
+    "pf_ess": (_INT, [_VP, _I64, _VP, _VP, _VP]),
+    "pf_resample_batched": (_INT, [_INT, _VP, _VP, _INT, _INT, _VP, _VP, _VP]),
+    "pf_reserve": (_INT, [_I64, _I64, _INT, _VP]),
+    "pf_get_device_status": (_INT, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "pf_metropolis_B": (_I64, [_I64, ctypes.c_double, ctypes.c_double]),
+    "pf_status_string": (ctypes.c_char_p, [_INT]),
+    "pf_set_wait_limit_ns": (_INT, [_U64]),
+    "pf_debug_skip_publish": (_INT, [_I64]),
+    "pf_version": (_INT, []),
+}
+
+
+class PFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpf.so (once).  Raises OSError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"libpf.so not built at {path}; run python -m paper_1202_6163_gb300.build")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(st: int, where: str):
+    if st != PF_OK:
+        raise PFError(st, where)
+
+
+def pf_resample_systematic(logw, P, B, seed, ancestors, stream=None):
+    _check(load().pf_resample_systematic(_ptr(logw), P, B, seed, _ptr(ancestors), _stream(stream)),
+           "pf_resample_systematic")
+
+
+def pf_resample_stratified(logw, P, B, seed, ancestors, stream=None):
+    _check(load().pf_resample_stratified(_ptr(logw), P, B, seed, _ptr(ancestors), _stream(stream)),
+           "pf_resample_stratified")
+
+
+def pf_resample_multinomial(logw, P, B, seed, ancestors, stream=None):
+    _check(load().pf_resample_multinomial(_ptr(logw), P, B, seed, _ptr(ancestors), _stream(stream)),
+           "pf_resample_multinomial")
+
+
+def pf_resample_metropolis(logw, P, B, seed, ancestors, stream=None):
+    _check(load().pf_resample_metropolis(_ptr(logw), P, B, seed, _ptr(ancestors), _stream(stream)),
+           "pf_resample_metropolis")
+
+
+def pf_gather(src, P_src, row_bytes, ancestors, P_dst, dst, stream=None):
+    _check(load().pf_gather(_ptr(src), P_src, row_bytes, _ptr(ancestors), P_dst, _ptr(dst), _stream(stream)),
+           "pf_gather")
+
+
+def pf_ess(logw, P, ess_out, log_sum_out=None, stream=None):
+    _check(load().pf_ess(_ptr(logw), P, _ptr(ess_out), _ptr(log_sum_out), _stream(stream)), "pf_ess")
+
+
+def pf_resample_batched(kind, logw, offsets, F, B, seeds, ancestors, stream=None):
+    _check(load().pf_resample_batched(kind, _ptr(logw), _ptr(offsets), F, B, _ptr(seeds), _ptr(ancestors),
+                                      _stream(stream)), "pf_resample_batched")
+
+
+def pf_reserve(P_max, total_max=0, F_max=0, stream=None):
+    _check(load().pf_reserve(P_max, total_max, F_max, _stream(stream)), "pf_reserve")
+
+
+def pf_get_device_status(stream=None) -> int:
+    out = ctypes.c_int(0)
+    _check(load().pf_get_device_status(_stream(stream), ctypes.byref(out)), "pf_get_device_status")
+    return out.value
+
+
+def pf_metropolis_B(P, w_max, eps=0.01) -> int:
+    return int(load().pf_metropolis_B(P, w_max, eps))
+
+
+def pf_status_string(status: int) -> str:
+    return load().pf_status_string(status).decode()
+
+
+def pf_set_wait_limit_ns(ns: int):
+    _check(load().pf_set_wait_limit_ns(ns), "pf_set_wait_limit_ns")
+
+
+def pf_debug_skip_publish(tile: int):
+    _check(load().pf_debug_skip_publish(tile), "pf_debug_skip_publish")
+
+
+def pf_version() -> int:
+    return int(load().pf_version())
+
+
+# The four resamplers by kind, as the batched call numbers them.
+RESAMPLERS = {
+    PF_MULTINOMIAL: pf_resample_multinomial,
+    PF_STRATIFIED: pf_resample_stratified,
+    PF_SYSTEMATIC: pf_resample_systematic,
+    PF_METROPOLIS: pf_resample_metropolis,
+}

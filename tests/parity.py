@@ -1,0 +1,139 @@
+"""Comparison of GPU ancestors with the FP64 oracle under the near-tie rule.
+
+The rule: GPU ancestors must equal the oracle's, except at decisions whose
+uniform lies within TAU = 1e-6 (relative) of a cumulative-weight or
+weight-ratio threshold.  Read concretely:
+
+* cumulative schemes -- decision j compares its normalised position
+  x_j ((j+u)/P systematic, (j+u_j)/P stratified, u_j multinomial) with the
+  normalised cumulative weights theta_b = c_b / W.  A mismatch a_gpu != a_orc
+  is excused only if EVERY threshold theta_b the two picks disagree on
+  (b in [min, max) of the two picks) satisfies |x_j - theta_b| <= TAU theta_b,
+  and the GPU pick has positive weight.
+* Metropolis -- step b of chain i compares u_b with r = exp(lw_j - lw_k).  A
+  chain whose final state differs is excused only if flipping some of its
+  near-tie decisions (|u_b - r| <= TAU r) in the oracle's replay reaches the
+  GPU's final state.
+
+Every excused mismatch is listed; anything else fails.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+import oracle
+
+TAU = 1e-6
+
+
+@dataclass
+class ParityReport:
+    n: int
+    mismatches: int = 0
+    excused: list = field(default_factory=list)
+    failures: list = field(default_factory=list)
+    in_band: int = 0
+
+    @property
+    def ok(self):
+        return not self.failures
+
+    def summary(self):
+        return (f"n={self.n} mismatches={self.mismatches} excused={len(self.excused)} "
+                f"failures={len(self.failures)} in_band_decisions={self.in_band}")
+
+
+def positions(kind: str, lw: np.ndarray, seed: int, filter_id: int = 0) -> np.ndarray:
+    """Normalised positions x_j the oracle's cumulative decisions use."""
+    P = lw.size
+    j = np.arange(P, dtype=np.float64)
+    if kind == "systematic":
+        u = oracle.stream_uniforms(seed, filter_id, oracle.TAG_SYS, 1)[0]
+        return (j + u) / P
+    if kind == "stratified":
+        u = oracle.stream_uniforms(seed, filter_id, oracle.TAG_STRAT, P)
+        return (j + u) / P
+    if kind == "multinomial":
+        return oracle.stream_uniforms(seed, filter_id, oracle.TAG_MULTI, P, kind=1)
+    raise ValueError(kind)
+
+
+def check_cumulative(kind: str, lw, a_gpu, a_orc, seed: int = 0, filter_id: int = 0,
+                     tau: float = TAU, x=None) -> ParityReport:
+    """x: the normalised positions, if not those of the library's streams for `seed`."""
+    lw = np.asarray(lw, dtype=np.float32)
+    a_gpu = np.asarray(a_gpu).astype(np.int64)
+    a_orc = np.asarray(a_orc).astype(np.int64)
+    P = lw.size
+    rep = ParityReport(n=P)
+    if a_gpu.shape != a_orc.shape:
+        rep.failures.append(("shape", a_gpu.shape, a_orc.shape))
+        return rep
+    if np.any((a_gpu < 0) | (a_gpu >= P)):
+        bad = np.nonzero((a_gpu < 0) | (a_gpu >= P))[0][:10]
+        rep.failures.append(("out_of_range", bad.tolist(), a_gpu[bad].tolist()))
+        return rep
+    theta = oracle.normalised_cumsum(lw)
+    if x is None:
+        x = positions(kind, lw, seed, filter_id)
+    # decisions inside the band around the thresholds that bracket the oracle pick
+    hi_t = theta[a_orc]
+    lo_t = np.where(a_orc > 0, theta[np.maximum(a_orc - 1, 0)], 0.0)
+    near = (np.abs(x - hi_t) <= tau * hi_t) | ((a_orc > 0) & (np.abs(x - lo_t) <= tau * lo_t))
+    rep.in_band = int(near.sum())
+    mism = np.nonzero(a_gpu != a_orc)[0]
+    rep.mismatches = int(mism.size)
+    for j in mism:
+        g, o = int(a_gpu[j]), int(a_orc[j])
+        lo, hi = min(g, o), max(g, o)
+        th = theta[lo:hi]
+        tie = bool(np.all(np.abs(x[j] - th) <= tau * th)) and lw[g] > -np.inf
+        rec = (int(j), g, o, float(x[j]), float(th.min()) if th.size else float("nan"),
+               float(np.max(np.abs(x[j] - th) / th)) if th.size else float("nan"))
+        (rep.excused if tie else rep.failures).append(rec)
+    return rep
+
+
+def _replay(lw64, P, k, props, unifs, b0, flips_left, target, tau):
+    """Depth-first replay of a chain from step b0 in state k; True if target is reachable
+    by flipping at most flips_left near-tie decisions."""
+    for b in range(b0, len(props)):
+        j = int(props[b])
+        u = float(unifs[b])
+        if lw64[j] >= lw64[k]:
+            k = j
+            continue
+        r = math.exp(lw64[j] - lw64[k])
+        acc = u < r
+        if flips_left > 0 and abs(u - r) <= tau * r:
+            alt = k if acc else j
+            if _replay(lw64, P, alt, props, unifs, b + 1, flips_left - 1, target, tau):
+                return True
+        if acc:
+            k = j
+    return k == target
+
+
+def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TAU, max_flips=3) -> ParityReport:
+    """a_gpu, a_orc: ancestors of the chains listed in `chains` (all chains if None)."""
+    lw = np.asarray(lw, dtype=np.float32)
+    lw64 = lw.astype(np.float64)
+    P = lw.size
+    idx = np.arange(P) if chains is None else np.asarray(chains)
+    a_gpu = np.asarray(a_gpu).astype(np.int64)
+    a_orc = np.asarray(a_orc).astype(np.int64)
+    rep = ParityReport(n=idx.size)
+    if np.any((a_gpu < 0) | (a_gpu >= P)):
+        rep.failures.append(("out_of_range",))
+        return rep
+    mism = np.nonzero(a_gpu != a_orc)[0]
+    rep.mismatches = int(mism.size)
+    for q in mism:
+        i = int(idx[q])
+        props, unifs = oracle.metropolis_draws(seed, filter_id, P, i, B)
+        ok = _replay(lw64, P, i, props, unifs, 0, max_flips, int(a_gpu[q]), tau)
+        (rep.excused if ok else rep.failures).append((i, int(a_gpu[q]), int(a_orc[q])))
+    return rep

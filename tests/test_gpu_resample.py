@@ -1,0 +1,282 @@
+"""GPU parity: libpf (through its C ABI) against the FP64 oracle.
+
+Ancestors must match the oracle's exactly except at near-tie decisions (see
+tests/parity.py); gathered states bit for bit; ESS within the tolerance derived
+from the arithmetic (2e-6 relative: per-weight error of a few float ulps,
+compensated sums, an FP64 combine).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1202_6163_gb300 import pf, workloads
+from parity import check_cumulative, check_metropolis
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CUMULATIVE = {
+    "systematic": (pf.pf_resample_systematic, oracle.systematic),
+    "stratified": (pf.pf_resample_stratified, oracle.stratified),
+    "multinomial": (pf.pf_resample_multinomial, oracle.multinomial),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    pf.load()
+    yield
+    torch.cuda.synchronize()
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def gpu_resample(fn, lw, seed, B=0):
+    t = to_dev(lw)
+    a = torch.full((lw.size,), -7, dtype=torch.int32, device="cuda")
+    fn(t, lw.size, B, seed, a)
+    st = pf.pf_get_device_status()
+    return a.cpu().numpy(), st
+
+
+def assert_cumulative(kind, lw, seed):
+    fn, orc = CUMULATIVE[kind]
+    a, st = gpu_resample(fn, lw, seed)
+    assert st == pf.PF_OK, pf.pf_status_string(st)
+    rep = check_cumulative(kind, lw, a, orc(lw, seed), seed)
+    assert rep.ok, rep.summary() + f" first failures: {rep.failures[:5]}"
+    if kind != "multinomial":
+        assert np.all(np.diff(a) >= 0)
+    return rep
+
+
+# ------------------------------------------------------------------ workload: P = 1024
+def test_single_resample_P1024_all_four_and_gather():
+    P = 1024
+    lw = workloads.gaussian_logw(P, 1.0, seed=0)
+    states = workloads.states(P, 4, seed=1)
+    for kind in CUMULATIVE:
+        assert_cumulative(kind, lw, 0)
+    a, st = gpu_resample(pf.pf_resample_metropolis, lw, 0, B=64)
+    assert st == pf.PF_OK
+    rep = check_metropolis(lw, 64, a, oracle.metropolis(lw, 64, 0), 0)
+    assert rep.ok, rep.summary()
+    src = to_dev(states)
+    dst = torch.empty_like(src)
+    anc = to_dev(a.astype(np.int32))
+    pf.pf_gather(src, P, 16, anc, P, dst)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    assert np.array_equal(dst.cpu().numpy(), oracle.gather(states, a))
+
+
+# ------------------------------------------------------------------ sizes, tiles, ragged tails
+SIZES = [1, 2, 3, 4, 5, 31, 1000, 2048, 4097, 65539, 300001]
+
+
+@pytest.mark.parametrize("kind", list(CUMULATIVE))
+@pytest.mark.parametrize("P", SIZES)
+@pytest.mark.parametrize("s", [0.25, 1.0, 4.0])
+def test_cumulative_sizes(kind, P, s):
+    lw = workloads.gaussian_logw(P, s, seed=P + int(10 * s))
+    assert_cumulative(kind, lw, seed=P * 7 + 1)
+
+
+@pytest.mark.parametrize("kind", list(CUMULATIVE))
+@pytest.mark.parametrize("s", [0.25, 1.0, 2.0, 4.0])
+def test_cumulative_P2e20(kind, s):
+    P = 1 << 20
+    lw = workloads.gaussian_logw(P, s, seed=int(100 * s))
+    rep = assert_cumulative(kind, lw, seed=11)
+    print(kind, s, rep.summary())
+
+
+@pytest.mark.parametrize("P", [1, 3, 1000, 65539])
+@pytest.mark.parametrize("B", [0, 1, 7, 64])
+def test_metropolis_sizes(P, B):
+    lw = workloads.gaussian_logw(P, 1.0, seed=P + B)
+    a, st = gpu_resample(pf.pf_resample_metropolis, lw, 5, B=B)
+    assert st == pf.PF_OK
+    rep = check_metropolis(lw, B, a, oracle.metropolis(lw, B, 5), 5)
+    assert rep.ok, rep.summary()
+
+
+@pytest.mark.parametrize("s,B", [(0.25, 8), (1.0, 32), (2.0, 128), (4.0, 512)])
+def test_metropolis_P2e20_sampled(s, B):
+    P = 1 << 20
+    lw = workloads.gaussian_logw(P, s, seed=int(100 * s))
+    a, st = gpu_resample(pf.pf_resample_metropolis, lw, 21, B=B)
+    assert st == pf.PF_OK
+    idx = np.random.default_rng(0).choice(P, size=2000, replace=False)
+    idx = np.concatenate([idx, [0, 1, P - 1]])
+    rep = check_metropolis(lw, B, a[idx], oracle.metropolis(lw, B, 21, chains=idx), 21, chains=idx)
+    assert rep.ok, rep.summary()
+    print("metropolis", s, B, rep.summary())
+
+
+# ------------------------------------------------------------------ edge cases
+def test_zero_weights_never_selected():
+    rng = np.random.default_rng(3)
+    for P in (7, 5000, 100003):
+        lw = rng.standard_normal(P).astype(np.float32)
+        lw[rng.random(P) < 0.3] = -np.inf
+        for kind in CUMULATIVE:
+            assert_cumulative(kind, lw, seed=P)
+        a, st = gpu_resample(pf.pf_resample_metropolis, lw, 1, B=16)
+        assert st == pf.PF_OK
+        assert check_metropolis(lw, 16, a, oracle.metropolis(lw, 16, 1), 1).ok
+
+
+def test_one_hot_and_equal_weights():
+    for P in (1, 9, 70001):
+        lw = np.full(P, -np.inf, np.float32)
+        lw[P // 3] = 1.5
+        for kind, (fn, _) in CUMULATIVE.items():
+            a, st = gpu_resample(fn, lw, 2)
+            assert st == pf.PF_OK and np.all(a == P // 3), kind
+        eq = np.full(P, -3.25, np.float32)
+        for kind in ("systematic", "stratified"):
+            a, st = gpu_resample(CUMULATIVE[kind][0], eq, 4)
+            assert st == pf.PF_OK and np.array_equal(a, np.arange(P)), kind
+
+
+def test_extreme_log_weights():
+    rng = np.random.default_rng(5)
+    P = 200003
+    for lw in (rng.standard_normal(P).astype(np.float32) - 5000.0,
+               (30.0 * rng.standard_normal(P)).astype(np.float32),
+               np.linspace(-80, 80, P).astype(np.float32)):
+        for kind in CUMULATIVE:
+            assert_cumulative(kind, lw, seed=9)
+
+
+def test_deterministic_and_seed_sensitive():
+    lw = workloads.gaussian_logw(100000, 1.0, seed=8)
+    for kind, (fn, _) in CUMULATIVE.items():
+        a1, _ = gpu_resample(fn, lw, 123)
+        a2, _ = gpu_resample(fn, lw, 123)
+        a3, _ = gpu_resample(fn, lw, 124)
+        assert np.array_equal(a1, a2)
+        assert not np.array_equal(a1, a3)
+
+
+def test_philox_streams_visible_through_equal_weights():
+    # with equal weights and P = 2^k the multinomial pick is floor(u_j P) and the
+    # Metropolis pick is the last proposal: both expose the raw Philox words
+    P = 1 << 12
+    lw = np.zeros(P, np.float32)
+    a, _ = gpu_resample(pf.pf_resample_multinomial, lw, 77)
+    u = oracle.stream_uniforms(77, 0, oracle.TAG_MULTI, P, kind=1)
+    assert np.array_equal(a, np.floor(u * P).astype(np.int64))
+    a, _ = gpu_resample(pf.pf_resample_metropolis, lw, 78, B=5)
+    last = [oracle.metropolis_draws(78, 0, P, i, 5)[0][-1] for i in range(P)]
+    assert np.array_equal(a, last)
+
+
+# ------------------------------------------------------------------ errors
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_domain_errors(bad):
+    lw = workloads.gaussian_logw(50000, 1.0, seed=1)
+    lw[1234] = bad
+    for kind, (fn, _) in CUMULATIVE.items():
+        _, st = gpu_resample(fn, lw, 0)
+        assert st == pf.PF_ERR_DOMAIN, kind
+    _, st = gpu_resample(pf.pf_resample_metropolis, lw, 0, B=4)
+    assert st == pf.PF_ERR_DOMAIN
+    e = torch.zeros(1, device="cuda")
+    pf.pf_ess(to_dev(lw), lw.size, e)
+    assert pf.pf_get_device_status() == pf.PF_ERR_DOMAIN
+
+
+def test_all_zero_weights_is_domain_error():
+    lw = np.full(3000, -np.inf, np.float32)
+    for kind, (fn, _) in CUMULATIVE.items():
+        _, st = gpu_resample(fn, lw, 0)
+        assert st == pf.PF_ERR_DOMAIN, kind
+
+
+def test_invalid_arguments():
+    t = torch.zeros(17, device="cuda")
+    a = torch.zeros(17, dtype=torch.int32, device="cuda")
+    for fn in list(pf.RESAMPLERS.values()):
+        with pytest.raises(pf.PFError) as ei:
+            fn(t, 0, 1, 0, a)
+        assert ei.value.status == pf.PF_ERR_INVALID
+        with pytest.raises(pf.PFError):
+            fn(t.data_ptr() + 4, 16, 1, 0, a)  # misaligned log-weights
+        with pytest.raises(pf.PFError):
+            fn(0, 16, 1, 0, a)
+    with pytest.raises(pf.PFError):
+        pf.pf_gather(t, 17, 6, a, 1, torch.zeros(17, device="cuda"))
+    with pytest.raises(pf.PFError):
+        pf.pf_gather(t, 17, 4, a, 4, t)  # overlapping
+
+
+def test_timeout_is_reported_and_recovered():
+    P = 1 << 20
+    lw = workloads.gaussian_logw(P, 1.0, seed=2)
+    pf.pf_set_wait_limit_ns(20_000_000)
+    try:
+        pf.pf_debug_skip_publish(3)
+        _, st = gpu_resample(pf.pf_resample_systematic, lw, 1)
+        assert st == pf.PF_ERR_TIMEOUT
+    finally:
+        pf.pf_debug_skip_publish(-1)
+        pf.pf_set_wait_limit_ns(1_000_000_000)
+    assert_cumulative("systematic", lw, 1)
+
+
+# ------------------------------------------------------------------ ESS and gather
+@pytest.mark.parametrize("P", [1, 5, 4096, 4099, 1 << 20])
+@pytest.mark.parametrize("s", [0.25, 1.0, 4.0])
+def test_ess(P, s):
+    lw = workloads.gaussian_logw(P, s, seed=P)
+    e = torch.zeros(1, device="cuda")
+    ls = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pf.pf_ess(to_dev(lw), P, e, ls)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    ess, log_sum = oracle.ess(lw)
+    assert e.item() == pytest.approx(ess, rel=2e-6)
+    assert ls.item() == pytest.approx(log_sum, rel=1e-12, abs=2e-6)
+
+
+@pytest.mark.parametrize("row_bytes", [4, 12, 16, 64, 68, 256])
+@pytest.mark.parametrize("P", [1, 1000, 70001])
+def test_gather_bit_exact(row_bytes, P):
+    rng = np.random.default_rng(row_bytes + P)
+    src = rng.integers(0, 2**31, size=(P, row_bytes // 4), dtype=np.int64).astype(np.int32)
+    P_dst = P + 3
+    anc = rng.integers(0, P, size=P_dst).astype(np.int32)
+    d_src = to_dev(src)
+    d_dst = torch.zeros((P_dst, row_bytes // 4), dtype=torch.int32, device="cuda")
+    pf.pf_gather(d_src, P, row_bytes, to_dev(anc), P_dst, d_dst)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    assert np.array_equal(d_dst.cpu().numpy(), oracle.gather(src, anc))
+
+
+def test_gather_rejects_out_of_range_ancestor():
+    src = torch.arange(40, dtype=torch.int32, device="cuda").reshape(10, 4)
+    dst = torch.full((3, 4), -1, dtype=torch.int32, device="cuda")
+    anc = torch.tensor([2, 10, 0], dtype=torch.int32, device="cuda")
+    pf.pf_gather(src, 10, 16, anc, 3, dst)
+    assert pf.pf_get_device_status() == pf.PF_ERR_INVALID
+    out = dst.cpu().numpy()
+    assert np.array_equal(out[0], [8, 9, 10, 11]) and np.all(out[1] == -1) and np.array_equal(out[2], [0, 1, 2, 3])
+
+
+def test_metropolis_autotuned_B():
+    P = 4096
+    lw = workloads.gaussian_logw(P, 1.0, seed=6)
+    ess, log_sum = oracle.ess(lw)
+    w_max = float(np.exp(np.float64(lw.max()) - log_sum))
+    B = oracle.metropolis_B(P, w_max, 0.01)
+    a, st = gpu_resample(pf.pf_resample_metropolis, lw, 3, B=-1)
+    assert st == pf.PF_OK
+    # the device derives w_max from its own float sums: B may differ by one at a rounding edge
+    matches = [b for b in (B - 1, B, B + 1) if np.array_equal(a, gpu_resample(pf.pf_resample_metropolis, lw, 3, b)[0])]
+    assert B in matches or matches, (B, matches)
+    assert check_metropolis(lw, B, gpu_resample(pf.pf_resample_metropolis, lw, 3, B)[0],
+                            oracle.metropolis(lw, B, 3), 3).ok
