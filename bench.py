@@ -1,0 +1,455 @@
+"""Benchmark of the resampling stage on GB300 (one JSON line on rank 0).
+
+Workload: one filter of P = 2^20 particles, log-weights N(0, 1) (float32),
+states P x 16 float32.  One step runs the whole single-filter hot path on that
+input through the C ABI: ESS, systematic, stratified, multinomial and
+Metropolis (B = 32) resampling, and the ancestor gather of the states (by the
+systematic ancestors).  value = ancestors produced per second (4 P per step).
+
+Timing: W untimed warm-up steps, then K steps timed on the device with CUDA
+events on the launching stream; before each step a short device-side sleep
+lets the host queue the step's launches, and L2 is flushed (a 256 MiB write,
+outside the timed interval) between steps.  Per-kernel durations come from
+events around each launch.  N > 1 (torchrun): independent replicas, one per
+GPU, max time over ranks.
+
+--impl reference times the FP64 CPU oracle (the project's reference
+implementation of the same method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P_DEFAULT = 1 << 20
+D_STATE = 16
+METRO_B = 32
+SPREAD = 1.0
+SEED = 0
+METRIC = "ancestors/s at P=2^20 (%HBM peak); batched filters/s vs per-filter launches"
+UNIT = "ancestors/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """dram bytes per launch recorded by the committed ncu summary, if the kernel's
+    sources have not changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d[kernel]
+        if source_hash(e["sources"]) != e["source_hash"]:
+            return None
+        return float(e["dram_bytes_per_launch"]) * float(e.get("scale_to_bench", 1.0))
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1202_6163_gb300 import pf, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pf.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    P = args.P
+    lw_h = workloads.gaussian_logw(P, SPREAD, seed=SEED + rank)
+    st_h = workloads.states(P, D_STATE, seed=SEED + 1 + rank)
+    lw = torch.from_numpy(lw_h).to(dev)
+    src = torch.from_numpy(st_h).to(dev)
+    dst = torch.empty_like(src)
+    anc = {k: torch.empty(P, dtype=torch.int32, device=dev) for k in ("sys", "strat", "multi", "metro")}
+    ess = torch.zeros(1, device=dev)
+    log_sum = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    pf.pf_reserve(P, 0, 0, stream)
+    row_bytes = D_STATE * 4
+    seed_box = [SEED]
+
+    kernels = ["ess", "systematic", "stratified", "multinomial", "metropolis", "gather"]
+
+    def step(evs=None):
+        s = seed_box[0]
+        seed_box[0] += 1
+
+        def mark(i):
+            if evs is not None:
+                evs[i].record(stream)
+
+        mark(0)
+        pf.pf_ess(lw, P, ess, log_sum, stream)
+        mark(1)
+        pf.pf_resample_systematic(lw, P, 0, s, anc["sys"], stream)
+        mark(2)
+        pf.pf_resample_stratified(lw, P, 0, s, anc["strat"], stream)
+        mark(3)
+        pf.pf_resample_multinomial(lw, P, 0, s, anc["multi"], stream)
+        mark(4)
+        pf.pf_resample_metropolis(lw, P, METRO_B, s, anc["metro"], stream)
+        mark(5)
+        pf.pf_gather(src, P, row_bytes, anc["sys"], P, dst, stream)
+        mark(6)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if pf.pf_get_device_status(stream) != pf.PF_OK:
+        raise RuntimeError("device status not OK after warm-up")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    per_kernel = {k: 0.0 for k in kernels}
+    total_ms = 0.0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    ev_sets = []
+    for _ in range(args.steps):
+        flush.zero_()  # evict L2 (outside the timed interval)
+        torch.cuda._sleep(20000)  # let the host queue the step's launches
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        step(evs)
+        ev_sets.append(evs)
+        if len(ev_sets) >= 64:
+            torch.cuda.synchronize(dev)
+            for e in ev_sets:
+                total_ms += e[0].elapsed_time(e[6])
+                for i, k in enumerate(kernels):
+                    per_kernel[k] += e[i].elapsed_time(e[i + 1])
+            ev_sets = []
+    torch.cuda.synchronize(dev)
+    for e in ev_sets:
+        total_ms += e[0].elapsed_time(e[6])
+        for i, k in enumerate(kernels):
+            per_kernel[k] += e[i].elapsed_time(e[i + 1])
+    wall = time.perf_counter() - wall0
+    time.sleep(0.2)
+    clocks = sampler.stop()
+    status = pf.pf_get_device_status(stream)
+    if status != pf.PF_OK:
+        raise RuntimeError(f"device status {status} after the timed steps")
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    ms_per_step = total_ms / args.steps
+    ancestors_per_step = 4 * P
+    value = world * ancestors_per_step * args.steps / (total_ms / 1e3)
+
+    hbm_peak, peak_kind = load_peaks()
+    # algorithmic bytes per launch
+    alg = {
+        "ess": 4 * P,
+        "systematic": 8 * P,
+        "stratified": 8 * P,
+        "multinomial": 8 * P,
+        "metropolis": 8 * P,
+        "gather": (2 * row_bytes + 4) * P,
+    }
+    breakdown = {}
+    for k in kernels:
+        us = per_kernel[k] / args.steps * 1e3
+        gbs = alg[k] / (us * 1e-6) / 1e9
+        breakdown[k] = {"us": round(us, 3), "algorithmic_bytes": alg[k], "achieved_gbs": round(gbs, 1),
+                        "hbm_frac": round(gbs / hbm_peak, 4), "share": round(per_kernel[k] / total_ms, 4)}
+    dominant = max(kernels, key=lambda k: per_kernel[k])
+    sources = {"systematic": "pf_persistent.cu", "stratified": "pf_persistent.cu",
+               "multinomial": "pf_persistent.cu", "metropolis": "pf_metropolis.cu", "gather": "pf_misc.cu",
+               "ess": "pf_misc.cu"}
+    dk = breakdown[dominant]
+    roofline = {"kernel": dominant, "bound": "hbm", "achieved": dk["achieved_gbs"], "peak": hbm_peak,
+                "unit": "GB/s", "frac": dk["hbm_frac"], "traffic": profiled_traffic(dominant),
+                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    if dominant == "metropolis":
+        steps_per_s = P * METRO_B / (dk["us"] * 1e-6)
+        roofline.update({"bound": "alu", "achieved": round(steps_per_s / 1e9, 2), "unit": "Gsteps/s",
+                         "peak": None, "frac": None,
+                         "note": "Philox-bound chain steps; peak derived in DESIGN.md"})
+    headline = breakdown["systematic"]
+
+    e2e = run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes) if not args.no_e2e else None
+
+    launches_per_step = 6 + 0  # one kernel per entry point (the autotuned-B reduction is not used here)
+    out = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "single filter P=2^20, log-weights N(0,1) f32, states Px16 f32; "
+                               "ess + systematic + stratified + multinomial + metropolis(B=32) + gather",
+                   "P": P, "state_dim": D_STATE, "metropolis_B": METRO_B, "spread": SPREAD,
+                   "l2": "flushed between steps (256 MiB write, outside the timed interval)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "headline_systematic": {"ancestors_per_s": round(P / (headline["us"] * 1e-6), 1),
+                                "us": headline["us"], "hbm_frac": headline["hbm_frac"],
+                                "achieved_gbs": headline["achieved_gbs"]},
+        "per_kernel": breakdown,
+        "gpu_launches": launches_per_step * args.steps,
+        "e2e": e2e,
+        "clocks": clocks,
+        "wall_s": round(wall, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes):
+    """Same step through the C ABI with host buffers: pinned H2D of the step's inputs,
+    the six calls, D2H of its outputs, all inside the timed interval."""
+    lw_p = torch.from_numpy(lw_h).pin_memory()
+    st_p = torch.from_numpy(st_h).pin_memory()
+    out_anc = torch.empty((4, P), dtype=torch.int32).pin_memory()
+    out_st = torch.empty_like(st_p).pin_memory()
+    out_ess = torch.empty(1).pin_memory()
+    lw = torch.empty(P, device=dev)
+    src = torch.empty((P, D_STATE), device=dev)
+    dst = torch.empty_like(src)
+    anc = torch.empty((4, P), dtype=torch.int32, device=dev)
+    ess = torch.zeros(1, device=dev)
+    steps = max(3, min(args.steps, 50))
+
+    def one(seed):
+        lw.copy_(lw_p, non_blocking=True)
+        src.copy_(st_p, non_blocking=True)
+        pf.pf_ess(lw, P, ess, None, stream)
+        pf.pf_resample_systematic(lw, P, 0, seed, anc[0], stream)
+        pf.pf_resample_stratified(lw, P, 0, seed, anc[1], stream)
+        pf.pf_resample_multinomial(lw, P, 0, seed, anc[2], stream)
+        pf.pf_resample_metropolis(lw, P, METRO_B, seed, anc[3], stream)
+        pf.pf_gather(src, P, row_bytes, anc[0], P, dst, stream)
+        out_anc.copy_(anc, non_blocking=True)
+        out_st.copy_(dst, non_blocking=True)
+        out_ess.copy_(ess, non_blocking=True)
+
+    for i in range(3):
+        one(1000 + i)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        one(2000 + i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    h2d = lw_p.numel() * 4 + st_p.numel() * 4
+    d2h = out_anc.numel() * 4 + out_st.numel() * 4 + 4
+    return {"value": round(4 * P / (ms * 1e-3), 1), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_step_time(P, metro_chains, seed):
+    """One step of the oracle over a bounded sample: the three cumulative resamplers, ESS
+    and the gather at full P; Metropolis on `metro_chains` chains (scaled to P)."""
+    import numpy as np
+
+    import oracle
+    from paper_1202_6163_gb300 import workloads
+    lw = workloads.gaussian_logw(P, SPREAD, seed=SEED)
+    st = workloads.states(P, D_STATE, seed=SEED + 1)
+    idx = np.arange(metro_chains, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.ess(lw)
+    a = oracle.systematic(lw, seed)
+    oracle.stratified(lw, seed)
+    oracle.multinomial(lw, seed)
+    t1 = time.perf_counter()
+    oracle.metropolis(lw, METRO_B, seed, chains=idx)
+    t2 = time.perf_counter()
+    oracle.gather(st, a)
+    t3 = time.perf_counter()
+    return (t1 - t0) + (t3 - t2) + (t2 - t1) * P / metro_chains
+
+
+def cpu_baseline(args, budget_s=None):
+    import oracle
+    oracle.build()
+    budget_s = budget_s if budget_s is not None else args.cpu_budget
+    P = args.P
+    chains = 1 << 14
+    t_total, n = 0.0, 0
+    wall0 = time.perf_counter()
+    while time.perf_counter() - wall0 < budget_s or n == 0:
+        t_total += oracle_step_time(P, chains, 100 + n)
+        n += 1
+    per_step = t_total / n
+    return {"value": round(4 * P / per_step, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle steps at P=2^20: ess, systematic, stratified, multinomial and the gather "
+                      f"in full; Metropolis (B={METRO_B}) on {chains} of the P chains, scaled to P",
+            "s_per_step": round(per_step, 4)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    P = args.P
+    chains = 1 << 12
+    for i in range(args.warmup):
+        oracle_step_time(P, chains, 10 + i)
+    times = [oracle_step_time(P, chains, 100 + i) for i in range(args.steps)]
+    per_step = sum(times) / len(times)
+    value = 4 * P / per_step
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(per_step * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "single filter P=2^20, log-weights N(0,1) f32, states Px16 f32; "
+                               "ess + systematic + stratified + multinomial + metropolis(B=32) + gather",
+                   "P": P, "state_dim": D_STATE, "metropolis_B": METRO_B, "spread": SPREAD,
+                   "parallelism": "single host thread"},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: the oracle at P=2^20 in full except Metropolis, run on {chains} "
+                                   f"chains and scaled to P"},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--P", type=int, default=P_DEFAULT)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

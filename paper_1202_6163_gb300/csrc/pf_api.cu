@@ -156,6 +156,7 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     p.lw = logw;
     p.anc = anc;
     p.P = P;
+    p.Pd = (double)P;
     p.tile = tile;
     p.n_tiles = G;
     p.key0 = (uint32_t)(seed & 0xffffffffu);

@@ -154,8 +154,84 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
     return v;
 }
 
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ uint64_t tag_slot(uint32_t epoch, uint32_t bits) {
     return ((uint64_t)epoch << 32) | bits;
+}
+
+// 16-byte loads and stores of two epoch-tagged words.  Each 8-byte word is
+// single-copy atomic and carries its own tag, so a reader that sees both tags
+// current has both values whatever the order the halves arrived in.
+__device__ __forceinline__ void ld_cg_v2(const uint64_t* p, uint64_t& a, uint64_t& b) {
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+__device__ __forceinline__ void st_v2(uint64_t* p, uint64_t a, uint64_t b) {
+    asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_v4_u32(uint32_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__device__ __forceinline__ uint4 ld_cg_v4_u32(const uint32_t* p) {
+    uint4 v;
+    asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+// Float-pair (double-float) arithmetic for the few per-tile scalars that need
+// more than float precision; FP64 issue on this part is far slower.
+__device__ __forceinline__ fpair fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ fpair pair_mul(fpair a, fpair b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ fpair pair_div(fpair a, fpair b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    // remainder a - q1 b, exactly enough for the second quotient digit
+    const float p = __fmul_rn(q1, b.hi);
+    const float pe = __fmaf_rn(q1, b.hi, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
+    return fast_two_sum(q1, __fdiv_rn(r, b.hi));
+}
+
+__device__ __forceinline__ fpair pair_sub_f(fpair a, float b) {
+    float s, e;
+    two_sum(a.hi, -b, s, e);
+    return fast_two_sum(s, __fadd_rn(e, a.lo));
+}
+
+// ceil and floor of a normalised pair below 2^24 in magnitude, as integers.
+__device__ __forceinline__ long long pair_ceil(fpair a) {
+    const float c = ceilf(a.hi);
+    if (c != a.hi) return (long long)c;
+    return (long long)a.hi + (long long)ceilf(a.lo);
+}
+
+__device__ __forceinline__ long long pair_floor(fpair a) {
+    const float f = floorf(a.hi);
+    if (f != a.hi) return (long long)f;
+    return (long long)a.hi + (long long)floorf(a.lo);
 }
 
 // Spin (bounded) until *p carries epoch in its high word; returns false on timeout.

@@ -26,6 +26,8 @@ enum : int {
     CTL_QUEUE = 4,        // work-queue ticket of the batched kernels
     CTL_QUEUE_DONE = 5,   // completion counter of the batched kernels
     CTL_METRO_B = 6,      // Metropolis step count chosen on the device
+    CTL_ARRIVE0 = 8,      // arrival counters of the single-launch kernels,
+    CTL_ARRIVE1 = 9,      //   used by alternate epochs (one is reset while the other counts)
     CTL_WORDS = 16
 };
 
@@ -47,6 +49,7 @@ struct SortedParams {
     const float* lw;
     int32_t* anc;
     int64_t P;
+    double Pd;     // P as a double
     int tile;      // elements per tile (multiple of 4, <= kTileMax)
     int n_tiles;   // tiles (CTAs) of the launch
     uint32_t key0, key1, filter;

@@ -3,7 +3,7 @@
 // Metropolis step count (Section 2, Eqs. 1-5).
 #include <climits>
 
-#include "pf_device.cuh"
+#include "pf_fixed.cuh"
 
 namespace pf {
 
@@ -100,14 +100,11 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float w) {
     s = t;
 }
 
-__device__ __forceinline__ double metropolis_bound(double P, double w_max, double eps) {
-    const double beta = 1.0 / P;
-    const double alpha = (1.0 - w_max) / (P * w_max);
-    const double lambda = 1.0 - alpha - beta;
-    const double target = eps * (alpha + beta) / fmax(alpha, beta);
-    if (target >= 1.0) return 0.0;
-    if (lambda <= 0.0) return 1.0;
-    return ceil(log(target) / log(lambda));
+__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int o) {
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    return (i128)(((unsigned __int128)h2 << 64) | l2);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict__ lw, int64_t P, RedRecord* rec,
@@ -115,7 +112,10 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict_
                                                         uint32_t* B_out, double eps, uint32_t B_cap) {
     __shared__ float rm[kRedThreads / 32];
     __shared__ fpair rs[kRedThreads / 32], rq[kRedThreads / 32];
+    __shared__ int rk[kRedThreads / 32];
+    __shared__ i128 rS[kRedThreads / 32], rQ[kRedThreads / 32];
     __shared__ int last;
+    const float eps_f = (float)eps;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t t0 = (int64_t)blockIdx.x * kRedTile;
     const int n = (int)min((int64_t)kRedTile, P - t0);
@@ -193,51 +193,87 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict_
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // last CTA: combine the tiles in index order (FP64)
-    if (tid < 32) {
-        const int T = gridDim.x;
-        int kmax = INT_MIN, anybad = 0;
-        float mmax = -INFINITY;
-        for (int t = lane; t < T; t += 32) {
-            anybad |= (int)__ldcg(&rec[t].bad);
-            if (__ldcg(&rec[t].s_hi) > 0.f) kmax = max(kmax, __ldcg(&rec[t].k));
-            mmax = fmaxf(mmax, __ldcg(&rec[t].m));
-        }
-        kmax = warp_max_i(kmax);
-        anybad = __any_sync(0xffffffffu, anybad);
-        mmax = warp_max(mmax);
-        double S = 0.0, Q = 0.0;
-        if (!anybad && kmax != INT_MIN) {
-            for (int t = lane; t < T; t += 32) {
-                const int kk = __ldcg(&rec[t].k) - kmax;
-                S += ldexp((double)__ldcg(&rec[t].s_hi) + (double)__ldcg(&rec[t].s_lo), kk);
-                Q += ldexp((double)__ldcg(&rec[t].q_hi) + (double)__ldcg(&rec[t].q_lo), 2 * kk);
-            }
+    // last CTA: combine all tiles (exact fixed-point sums, all threads)
+    const int T = gridDim.x;
+    int kmax = INT_MIN, anybad = 0;
+    float mmax = -INFINITY;
+    for (int t = tid; t < T; t += kRedThreads) {
+        anybad |= (int)__ldcg(&rec[t].bad);
+        if (__ldcg(&rec[t].s_hi) > 0.f) kmax = max(kmax, __ldcg(&rec[t].k));
+        mmax = fmaxf(mmax, __ldcg(&rec[t].m));
+    }
+    kmax = warp_max_i(kmax);
+    mmax = warp_max(mmax);
+    if (lane == 0) {
+        rk[warp] = kmax;
+        rm[warp] = mmax;
+    }
+    anybad = __syncthreads_or(anybad);
+    int K = rk[0];
+    float M = rm[0];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                S += __shfl_xor_sync(0xffffffffu, S, o);
-                Q += __shfl_xor_sync(0xffffffffu, Q, o);
-            }
+    for (int w = 1; w < kRedThreads / 32; ++w) {
+        K = max(K, rk[w]);
+        M = fmaxf(M, rm[w]);
+    }
+    if (anybad || K == INT_MIN) {
+        if (tid == 0) {
+            set_status(ctl + CTL_STATUS, ST_DOMAIN);
+            if (ess_out) *ess_out = NAN;
+            if (log_sum_out) *log_sum_out = NAN;
+            if (B_out) *B_out = 0;
+            ctl[CTL_ESS_COUNT] = 0;
         }
-        if (lane == 0) {
-            if (anybad || kmax == INT_MIN) {
-                set_status(ctl + CTL_STATUS, ST_DOMAIN);
-                if (ess_out) *ess_out = NAN;
-                if (log_sum_out) *log_sum_out = NAN;
-                if (B_out) *B_out = 0;
+        return;
+    }
+    i128 S = 0, Q = 0;
+    for (int t = tid; t < T; t += kRedThreads) {
+        const int sh = __ldcg(&rec[t].k) - K;
+        S += fixed_of(__ldcg(&rec[t].s_hi), sh) + fixed_of(__ldcg(&rec[t].s_lo), sh);
+        Q += fixed_of(__ldcg(&rec[t].q_hi), 2 * sh) + fixed_of(__ldcg(&rec[t].q_lo), 2 * sh);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        S += shfl_xor_i128(S, o);
+        Q += shfl_xor_i128(Q, o);
+    }
+    if (lane == 0) {
+        rS[warp] = S;
+        rQ[warp] = Q;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < kRedThreads / 32; ++w) {
+            S += rS[w];
+            Q += rQ[w];
+        }
+        const fpair Sp = fixed_to_pair(S), Qp = fixed_to_pair(Q);
+        // ESS = S^2 / Q in float (first order in the low parts)
+        const float ratio = Sp.hi * (Sp.hi / Qp.hi);
+        const float corr = 2.f * (Sp.lo / Sp.hi) - Qp.lo / Qp.hi;
+        if (ess_out) *ess_out = __fmaf_rn(ratio, corr, ratio);
+        // log sum exp(lw) = K ln 2 + log S
+        const float logS = logf(Sp.hi) + Sp.lo / Sp.hi;
+        const double log_sum = (double)K * kLn2 + (double)logS;
+        if (log_sum_out) *log_sum_out = log_sum;
+        if (B_out) {
+            // Eq. 5 with the actual largest normalised weight
+            const float ls = (float)((double)K * kLn2 - (double)M) + logS;  // log W - m
+            const float w_max = fminf(1.f, expf(-ls));
+            float b;
+            if (!(w_max > 0.f)) {
+                b = (float)B_cap;
             } else {
-                const double log_sum = (double)kmax * kLn2 + log(S);
-                if (ess_out) *ess_out = (float)(S * S / Q);
-                if (log_sum_out) *log_sum_out = log_sum;
-                if (B_out) {
-                    const double w_max = fmin(1.0, exp((double)mmax - log_sum));
-                    double b = metropolis_bound((double)P, w_max, eps);
-                    if (!(b >= 0.0)) b = (double)B_cap;
-                    *B_out = (uint32_t)fmin(b, (double)B_cap);
-                }
+                const float beta = 1.f / (float)P;
+                const float alpha = (1.f - w_max) / ((float)P * w_max);
+                const float target = eps_f * (alpha + beta) / fmaxf(alpha, beta);
+                if (target >= 1.f) b = 0.f;
+                else b = ceilf(logf(target) / log1pf(-(alpha + beta)));
             }
-            ctl[CTL_ESS_COUNT] = 0;  // ready for the next reduction on this stream
+            if (!(b >= 0.f)) b = (float)B_cap;
+            *B_out = (uint32_t)fminf(b, (float)B_cap);
         }
+        ctl[CTL_ESS_COUNT] = 0;  // ready for the next reduction on this stream
     }
 }
 

@@ -1,32 +1,37 @@
 // Single-launch resamplers for the cumulative schemes (Figure 1a-c).
 //
 // One cooperative launch, one tile per CTA, every CTA resident:
-//   1. tile scan (pf_tile.cuh): the tile's weights, its local cumulative
-//      weights v_i in shared memory and its sum S_t relative to 2^{k_t};
-//   2. publish (k_t, S_t, i_last) in epoch-tagged 64-bit slots;
-//   3. one warp gathers every tile's slots (bounded wait), and forms the
-//      inter-tile carries B_t = sum_{t'<t} S_t' 2^{k_t'-K} in FP64 -- the same
-//      arithmetic in every CTA, so each tile boundary has one value that both
-//      neighbouring tiles see bit for bit, and W = B_T is the scan's own last
-//      prefix;
-//   4. systematic / stratified: the tile owns the offsets j whose position
-//      (j + u_j) W / P lies in [B_t, B_{t+1}) and assigns them to its
-//      elements by a merge path over (v_i, offsets), staged through shared
-//      memory and stored coalesced;
-//      multinomial: the tile's v_i were also written to global memory before
-//      publishing; the CTA draws a balanced slice of the P uniforms, finds the
-//      tile by binary search over B_t/W in shared memory and the element by
-//      binary search in that tile's v_i.
+//   1. tile scan (pf_tile.cuh): the tile's weights and, in registers, its
+//      local cumulative weights v_i; its sum S_t relative to 2^{k_t};
+//   2. publish (k_t, S_t, i_last) and arrive on an epoch's counter; one thread
+//      per CTA waits (bounded) until every tile has arrived;
+//   3. every CTA reads all tiles' words and forms the inter-tile carries
+//          B_t = sum_{t' < t} S_t' 2^{k_t' - K}
+//      as exact 128-bit fixed-point sums (2^-90 resolution relative to the
+//      largest tile reference 2^K).  Integer sums are exact and associative, so
+//      every CTA holds bit-identical boundaries, and W = B_T is the scan's own
+//      last prefix;
+//   4. systematic / stratified (Section 2: these schemes yield offspring
+//      counts): the tile owns the offsets j whose position (j + u_j) W / P lies
+//      in [B_t, B_{t+1}); each element counts the offsets below its cumulative
+//      weight, N_i, and its ancestor index fills [N_{i-1}, N_i): a run-length
+//      decode in shared memory (mark run starts, then a block max-scan), with
+//      no per-thread loops over run lengths, stored with 128-bit writes;
+//      multinomial: the tile's v_i were written to global memory before
+//      arriving; the CTA draws a balanced slice of the P uniforms, finds the
+//      tile by binary search over the boundaries and the element by binary
+//      search in that tile's v_i.
 // Every global write is bounded by [0, P) whatever the data; a NaN/+inf or
-// all-zero weight set records PF_ERR_DOMAIN and writes nothing.
+// all-zero weight set records PF_ERR_DOMAIN and writes no ancestors.
 #include <climits>
 
+#include "pf_fixed.cuh"
 #include "pf_tile.cuh"
 
 namespace pf {
 
-constexpr int kMaxTiles = 1024;
-constexpr int kIoCap = 4096;  // offsets per merge-path chunk
+constexpr int kMaxTiles = 2 * kThreads;  // two tiles read per thread
+constexpr int kIoCap = 8192;             // offsets per staging chunk
 
 enum { KIND_MULTI = 0, KIND_STRAT = 1, KIND_SYS = 2 };
 
@@ -34,289 +39,333 @@ struct PersistShared {
     TileShared tile;
     union {
         struct {
-            float tau[kIoCap];
-            int32_t out[kIoCap + 8];
+            int32_t out[kIoCap];
         } s;
         struct {
-            float bhi[kMaxTiles], blo[kMaxTiles], rho[kMaxTiles];
+            float bhi[kMaxTiles], blo[kMaxTiles], sc[kMaxTiles];
         } m;
     } u;
-    double Bs[kMaxTiles + 1];  // carries, units of 2^K
-    int kt[kMaxTiles];
     int il[kMaxTiles];
-    int jlo, jhi, K, abort;
-    float tau0, rho0;
-    double W;
+    i128 wsum[kWarps];
+    i128 Bl, Bh, Wt;
+    int red_k[kWarps];
+    int red_n[kWarps];
+    int noff, K, ok;
+    long long jlo;
+    float tau0, inv_rho, W_hi, W_lo;
 };
 
-// ---------------------------------------------------------------------------
-// Offset counts N(B) = #{j : position of offset j < B}, in FP64, from the
-// canonical boundary values (both neighbouring tiles get the same count).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t n_below_sys(double B, double W, int64_t P, double u) {
-    if (!(B > 0.0)) return 0;
-    if (B >= W) return P;
-    double c = ceil(B / W * (double)P - u);
-    c = fmin(fmax(c, 0.0), (double)P);
-    return (int64_t)c;
-}
-
-__device__ __forceinline__ double u23d(uint32_t x) { return (double)(((x >> 9) << 1) | 1u) * 0x1p-24; }
-
-__device__ __forceinline__ int64_t n_below_strat(double B, double W, int64_t P, uint32_t k0, uint32_t k1,
-                                                 uint32_t filter) {
-    if (!(B > 0.0)) return 0;
-    if (B >= W) return P;
-    const double y = B / W * (double)P;
-    const double fl = floor(y);
-    if (fl >= (double)P) return P;
-    if (fl < 0.0) return 0;
-    const int64_t j = (int64_t)fl;
-    const u32x4 r = philox((uint32_t)(j >> 2), 0u, filter, TAG_STRAT, k0, k1);
-    return j + (u23d(word_of(r, (int)(j & 3))) < y - fl ? 1 : 0);
-}
 
 // ---------------------------------------------------------------------------
-// Gather every tile's slots and form the carries (warp 0; identical in all
-// CTAs).  Returns false on timeout or a domain error (status recorded).
+// Arrival and carries.  Block-wide; identical results in every CTA.
 // ---------------------------------------------------------------------------
-__device__ bool gather_carries(const SortedParams& p, PersistShared& sm, float* tmp_hi, float* tmp_lo,
-                               uint32_t epoch, uint64_t t_start) {
-    const int lane = threadIdx.x & 31;
-    const int T = p.n_tiles;
-    bool ok = true;
-    int bad = 0;
-    int kmax = INT_MIN;
-    for (int t = lane; t < T; t += 32) {
-        uint32_t kb = 0, hb = 0, lb = 0, ib = 0;
-        ok = ok && wait_slot(&p.slots[4 * t + 0], epoch, t_start, p.wait_ns, kb);
-        ok = ok && wait_slot(&p.slots[4 * t + 1], epoch, t_start, p.wait_ns, hb);
-        ok = ok && wait_slot(&p.slots[4 * t + 2], epoch, t_start, p.wait_ns, lb);
-        ok = ok && wait_slot(&p.slots[4 * t + 3], epoch, t_start, p.wait_ns, ib);
-        if (!ok) break;
-        const float hi = __uint_as_float(hb);
-        sm.kt[t] = (int)kb;
-        sm.il[t] = (int)ib;
-        tmp_hi[t] = hi;
-        tmp_lo[t] = __uint_as_float(lb);
-        if (hi > 0.f) kmax = max(kmax, (int)kb);
-        bad |= !(hi <= 3.402823466e38f);  // a tile saw NaN/+inf
+// Publish the tile's 16-byte record (k, S_hi, S_lo, i_last), arrive on this
+// epoch's counter with release semantics, and wait (one thread, bounded)
+// until every tile has arrived.
+__device__ bool arrive_and_wait(const SortedParams& p, PersistShared& sm, const TileSummary& ts, uint32_t epoch,
+                                uint64_t t_start) {
+    const int tid = threadIdx.x;
+    const int t = blockIdx.x;
+    uint32_t* arrive = p.ctl + CTL_ARRIVE0 + (epoch & 1u);
+    if (tid == 0) {
+        if (t != p.skip_tile) {
+            st_v4_u32(reinterpret_cast<uint32_t*>(p.slots) + 4 * t, (uint32_t)ts.k,
+                      __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo), (uint32_t)ts.i_last);
+            red_release_add_u32(arrive, 1u);
+        }
+        int ok = 1;
+        for (uint32_t it = 1; ld_acquire_u32(arrive) < (uint32_t)p.n_tiles; ++it) {
+            if ((it & 7u) == 0u && global_ns() - t_start > p.wait_ns) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        sm.ok = ok;
     }
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) {
-        if (lane == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
-        return false;
+    __syncthreads();
+    return sm.ok != 0;
+}
+
+// Block exclusive scan of one int128 per thread; returns the exclusive prefix
+// and leaves the block total in sm.Wt.
+__device__ __forceinline__ i128 block_scan_i128(PersistShared& sm, i128 x) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const i128 inc = warp_scan_i128(x, lane);
+    if (lane == 31) sm.wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const i128 v = lane < kWarps ? sm.wsum[lane] : (i128)0;
+        const i128 vi = warp_scan_i128(v, lane);
+        if (lane < kWarps) sm.wsum[lane] = vi - v;
+        if (lane == kWarps - 1) sm.Wt = vi;
+    }
+    __syncthreads();
+    return sm.wsum[warp] + (inc - x);
+}
+
+template <int KIND>
+__device__ bool carries(const SortedParams& p, PersistShared& sm, int my_tile) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = p.n_tiles;
+    const uint32_t* slots = reinterpret_cast<const uint32_t*>(p.slots);
+    // thread tid owns tiles tid and tid + kThreads; coalesced 16-byte reads
+    uint4 r[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        if (tid + q * kThreads < T) r[q] = ld_cg_v4_u32(slots + 4 * (tid + q * kThreads));
+    int bad = 0, kmax = INT_MIN;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (tid + q * kThreads < T) {
+            const float sh = __uint_as_float(r[q].y);
+            bad |= !(sh <= 3.402823466e38f);  // a tile saw NaN/+inf
+            if (sh > 0.f) kmax = max(kmax, (int)r[q].x);
+        } else {
+            r[q].y = 0u;
+            r[q].z = 0u;
+        }
     }
     kmax = warp_max_i(kmax);
-    bad = __any_sync(0xffffffffu, bad);
-    if (kmax == INT_MIN || bad) {  // every weight zero, or a bad tile
-        if (lane == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
+    if (lane == 0) sm.red_k[warp] = kmax;
+    bad = __syncthreads_or(bad);
+    int K = sm.red_k[0];
+#pragma unroll
+    for (int q = 1; q < kWarps; ++q) K = max(K, sm.red_k[q]);
+    if (K == INT_MIN || bad) {  // every weight zero, or a bad tile
+        if (tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
         return false;
     }
-    // contiguous groups of tiles per lane; exclusive FP64 scan
-    const int g = (T + 31) / 32;
-    const int t_beg = min(T, lane * g), t_end = min(T, t_beg + g);
-    double part = 0.0;
-    for (int t = t_beg; t < t_end; ++t) {
-        const double a = ldexp((double)tmp_hi[t] + (double)tmp_lo[t], sm.kt[t] - kmax);
-        sm.Bs[t] = a;  // the tile's own mass, replaced below
-        part += a;
+    i128 base = 0;
+    for (int q = 0; q < 2 && q * kThreads < T; ++q) {
+        const int t = tid + q * kThreads;
+        const int sh = (int)r[q].x - K;
+        const i128 a = fixed_of(__uint_as_float(r[q].y), sh) + fixed_of(__uint_as_float(r[q].z), sh);
+        const i128 B = base + block_scan_i128(sm, a);  // carry of tile t
+        const i128 total = base + sm.Wt;
+        __syncthreads();  // sm.wsum / sm.Wt are reused by the next pass
+        if (t < T) {
+            if (KIND == KIND_MULTI) {
+                const fpair b = fixed_to_pair(B);
+                sm.u.m.bhi[t] = b.hi;
+                sm.u.m.blo[t] = b.lo;
+                sm.u.m.sc[t] = pow2f(-sh);
+                sm.il[t] = (int)r[q].w;
+            } else {
+                if (t == my_tile) sm.Bl = B;
+                if (t == my_tile + 1) sm.Bh = B;
+            }
+        }
+        base = total;
     }
-    const double inc = warp_scan_d(part, lane);
-    double run = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) run = 0.0;
-    for (int t = t_beg; t < t_end; ++t) {
-        const double a = sm.Bs[t];
-        sm.Bs[t] = run;
-        run += a;
+    if (tid == 0) {
+        sm.K = K;
+        sm.Wt = base;
+        if (KIND != KIND_MULTI && my_tile + 1 == T) sm.Bh = base;
+        const fpair Wp = fixed_to_pair(base);
+        sm.W_hi = Wp.hi;
+        sm.W_lo = Wp.lo;
     }
-    const double W = __shfl_sync(0xffffffffu, inc, 31);
-    if (lane == 0) {
-        sm.Bs[T] = W;
-        sm.W = W;
-        sm.K = kmax;
-    }
-    __syncwarp();
+    __syncthreads();
     return true;
 }
 
 // ---------------------------------------------------------------------------
-// Merge path of the tile's elements against a chunk of its offsets.
+// Offspring-count assignment (systematic, stratified).
 // ---------------------------------------------------------------------------
+// Per-tile scalars (thread 0), in float pairs: the tile's offset range and the
+// map from tile-local cumulative weight v to the offset coordinate
+// y = v * inv_rho + x0 (offsets counted from jlo).  P < 2^24 on this path.
 template <int KIND>
-__device__ __forceinline__ float offset_tau(const PersistShared& sm, int o_tile, int o_chunk) {
-    if (KIND == KIND_SYS) return fmaxf(0.f, __fmaf_rn((float)o_tile, sm.rho0, sm.tau0));
-    return sm.u.s.tau[o_chunk];
-}
-
-// first element in [0, n) with |v| > tau (n if none)
-__device__ __forceinline__ int first_above(const float* vs, int n, float tau) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (fabsf(vs[mid]) > tau) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
-}
-
-template <int KIND>
-__device__ void assign_chunk(PersistShared& sm, const float* vs, int n, int i_last, int c0, int nc, int shift,
-                             int32_t base_index) {
-    const int tid = threadIdx.x;
-    // element window: every offset of the chunk lands in [e_lo, e_hi]
-    const int e_lo = first_above(vs, n, offset_tau<KIND>(sm, c0, 0));
-    const int e_hi = first_above(vs, n, offset_tau<KIND>(sm, c0 + nc - 1, nc - 1));
-    const int ne = min(n, e_hi + 1) - e_lo;
-    const float* v = vs + e_lo;
-    const int L = ne + nc;
-    const int d0 = (int)((int64_t)tid * L / kThreads);
-    const int d1 = (int)((int64_t)(tid + 1) * L / kThreads);
-    // partition at diagonal d0: number of window elements consumed
-    int lo = max(0, d0 - nc), hi = min(d0, ne);
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int o = d0 - mid - 1;
-        if (fabsf(v[mid]) <= offset_tau<KIND>(sm, c0 + o, o)) lo = mid + 1;
-        else hi = mid;
-    }
-    int i = lo, o = d0 - lo;
-    for (int d = d0; d < d1; ++d) {
-        const bool take = (i < ne) && (o >= nc || fabsf(v[i]) <= offset_tau<KIND>(sm, c0 + o, o));
-        if (take) {
-            ++i;
-        } else {
-            int idx = e_lo + i;
-            if (idx >= n) idx = i_last;
-            else if (zero_flag(vs[idx])) idx = next_positive(vs, n, idx, i_last);
-            sm.u.s.out[o + shift] = base_index + idx;
-            ++o;
-        }
-    }
-}
-
-// Coalesced store of out[shift .. shift+nc) to anc[g0 .. g0+nc); anc + g0 - shift is 16-byte aligned.
-__device__ __forceinline__ void store_chunk(const PersistShared& sm, int32_t* anc, int64_t g0, int nc, int shift) {
-    int32_t* a0 = anc + (g0 - shift);
-    const int nvec = (shift + nc + 3) >> 2;
-    for (int q = threadIdx.x; q < nvec; q += kThreads) {
-        const int s0 = 4 * q;
-        if (s0 >= shift && s0 + 3 < shift + nc) {
-            *reinterpret_cast<int4*>(a0 + s0) = *reinterpret_cast<const int4*>(&sm.u.s.out[s0]);
-        } else {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int s = s0 + r;
-                if (s >= shift && s < shift + nc) a0[s] = sm.u.s.out[s];
+__device__ void tile_offsets(const SortedParams& p, PersistShared& sm, int k_tile) {
+    const fpair W = {sm.W_hi, sm.W_lo};
+    const fpair Bl = fixed_to_pair(sm.Bl), Bh = fixed_to_pair(sm.Bh);
+    const float Ph = (float)p.P;  // exact: P < 2^24
+    const fpair PW = pair_div({Ph, 0.f}, W);
+    const fpair yl = pair_mul(Bl, PW), yh = pair_mul(Bh, PW);  // B P / W
+    const bool last = sm.Bh >= sm.Wt;
+    long long jl, jh;
+    float x0;
+    if (KIND == KIND_SYS) {
+        const u32x4 r = philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1);
+        const float u = u23f(r.x);
+        const fpair dl = pair_sub_f(yl, u), dh = pair_sub_f(yh, u);
+        jl = (sm.Bl > 0) ? max(0LL, min((long long)p.P, pair_ceil(dl))) : 0;
+        jh = last ? p.P : max(0LL, min((long long)p.P, pair_ceil(dh)));
+        x0 = __fadd_rn(__fsub_rn(dl.hi, (float)jl), dl.lo);  // N(v) = ceil(v * inv_rho + x0)
+    } else {
+        jl = 0;
+        if (sm.Bl > 0) {
+            const long long f = pair_floor(yl);
+            if (f >= p.P) {
+                jl = p.P;
+            } else {
+                const float frac = __fadd_rn(__fsub_rn(yl.hi, (float)f), yl.lo);
+                const u32x4 r = philox((uint32_t)(f >> 2), 0u, p.filter, TAG_STRAT, p.key0, p.key1);
+                jl = f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0);
             }
         }
+        jh = p.P;
+        if (!last) {
+            const long long f = pair_floor(yh);
+            if (f < p.P) {
+                const float frac = __fadd_rn(__fsub_rn(yh.hi, (float)f), yh.lo);
+                const u32x4 r = philox((uint32_t)(f >> 2), 0u, p.filter, TAG_STRAT, p.key0, p.key1);
+                jh = max(0LL, f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0));
+            }
+        }
+        x0 = __fadd_rn(__fsub_rn(yl.hi, (float)jl), yl.lo);  // y(v) = v * inv_rho + x0
     }
+    sm.jlo = jl;
+    sm.noff = (int)max(0LL, jh - jl);
+    sm.tau0 = x0;
+    sm.inv_rho = PW.hi * pow2f(k_tile - sm.K);
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
-    const int tid = threadIdx.x;
-    const int t = blockIdx.x;
-    const uint64_t t_start = global_ns();
-    const uint32_t epoch = ld_relaxed_u32(p.ctl + CTL_EPOCH) + 1u;
-
-    const int64_t t0 = (int64_t)t * p.tile;
-    const int n = (int)min((int64_t)p.tile, p.P - t0);
-
-    const TileSummary ts = tile_scan(p.lw + t0, n, sm.tile);
-    if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
-
-    if (KIND == KIND_MULTI) {
-        // this tile's cumulative weights go to global memory for the searches
-        float* vg = p.v_out + t0;
-        for (int i = tid; i < n; i += kThreads) vg[i] = sm.tile.vs[i];
-        __threadfence();
-        __syncthreads();
-    }
-    if (tid == 0 && t != p.skip_tile) {
-        uint64_t* s = p.slots + 4 * t;
-        st_release_u64(s + 0, tag_slot(epoch, (uint32_t)ts.k));
-        st_release_u64(s + 1, tag_slot(epoch, __float_as_uint(ts.bad ? NAN : ts.S.hi)));
-        st_release_u64(s + 2, tag_slot(epoch, __float_as_uint(ts.S.lo)));
-        st_release_u64(s + 3, tag_slot(epoch, (uint32_t)ts.i_last));
-    }
-
-    if (tid < 32) {
-        const bool ok = gather_carries(p, sm, sm.u.m.bhi, sm.u.m.blo, epoch, t_start);
-        if (tid == 0) {
-            sm.abort = ok ? 0 : 1;
-            if (t == 0) atomicExch(p.ctl + CTL_EPOCH, epoch);
-            if (ok && KIND != KIND_MULTI) {
-                const double W = sm.W;
-                const double Bl = sm.Bs[t], Bh = sm.Bs[t + 1];
-                const double scale = ldexp(1.0, sm.K - ts.k);  // global units -> tile-local units
-                const double step = W / (double)p.P;
-                int64_t jl, jh;
-                if (KIND == KIND_SYS) {
-                    const u32x4 r = philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1);
-                    const double u = u23d(r.x);
-                    jl = n_below_sys(Bl, W, p.P, u);
-                    jh = n_below_sys(Bh, W, p.P, u);
-                    sm.tau0 = (float)((((double)jl + u) * step - Bl) * scale);
+__device__ void assign_offspring(const SortedParams& p, PersistShared& sm, TileThread& th, const TileSummary& ts,
+                                 int64_t t0) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int noff = sm.noff;
+    const long long jlo = sm.jlo;
+    const float x0 = sm.tau0, ir = sm.inv_rho;
+    // N_i: offsets of the tile below the element's cumulative weight (kept in v[] as int bits)
+    uint32_t cq = 0xffffffffu;
+    u32x4 cw = {0, 0, 0, 0};
+    int last_n = -1;
+#pragma unroll
+    for (int i = 0; i < kMaxPerThread; ++i) {
+        if (i < th.K && ((th.pos >> i) & 1u)) {
+            int n;
+            if (th.e0 + i == ts.i_last) {
+                n = noff;
+            } else if (KIND == KIND_SYS) {
+                const float x = __fmaf_rn(th.v[i], ir, x0);
+                n = x <= 0.f ? 0 : (x >= (float)noff ? noff : min(noff, (int)ceilf(x)));
+            } else {
+                const float y = __fmaf_rn(th.v[i], ir, x0);
+                if (y <= 0.f) {
+                    n = 0;
                 } else {
-                    jl = n_below_strat(Bl, W, p.P, p.key0, p.key1, p.filter);
-                    jh = n_below_strat(Bh, W, p.P, p.key0, p.key1, p.filter);
-                    sm.tau0 = (float)(((double)jl * step - Bl) * scale);
-                }
-                sm.rho0 = (float)(step * scale);
-                sm.jlo = (int)jl;
-                sm.jhi = (int)max(jl, jh);
-            }
-        }
-    }
-    __syncthreads();
-    if (sm.abort) return;
-
-    if (KIND != KIND_MULTI) {
-        const int jlo = sm.jlo, jhi = sm.jhi;
-        for (int c0 = 0; c0 < jhi - jlo; c0 += kIoCap) {
-            const int nc = min(kIoCap, jhi - jlo - c0);
-            const int shift = (jlo + c0) & 3;
-            if (KIND == KIND_STRAT) {
-                // position (j + u_j) W/P of each offset of the chunk, tile-local units
-                const int64_t j0 = (int64_t)jlo + c0;
-                const int64_t q0 = j0 >> 2, q1 = (j0 + nc - 1) >> 2;
-                for (int64_t q = q0 + tid; q <= q1; q += kThreads) {
-                    const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_STRAT, p.key0, p.key1);
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        const int64_t j = 4 * q + s;
-                        if (j >= j0 && j < j0 + nc) {
-                            const float base = __fmaf_rn((float)(j - jlo), sm.rho0, sm.tau0);
-                            sm.u.s.tau[(int)(j - j0)] = fmaxf(0.f, __fmaf_rn(u23f(word_of(r, s)), sm.rho0, base));
+                    const float fl = floorf(y);
+                    if (fl >= (float)noff) {
+                        n = noff;
+                    } else {
+                        const long long j = jlo + (long long)fl;
+                        const uint32_t q = (uint32_t)(j >> 2);
+                        if (q != cq) {
+                            cq = q;
+                            cw = philox(q, 0u, p.filter, TAG_STRAT, p.key0, p.key1);
                         }
+                        n = min(noff, (int)fl + (u23f(word_of(cw, (int)(j & 3))) < y - fl ? 1 : 0));
                     }
                 }
-                __syncthreads();
             }
-            assign_chunk<KIND>(sm, sm.tile.vs, n, ts.i_last, c0, nc, shift, (int32_t)t0);
-            __syncthreads();
-            store_chunk(sm, p.anc, (int64_t)jlo + c0, nc, shift);
-            __syncthreads();
+            th.v[i] = __int_as_float(n);
+            last_n = n;
         }
-        return;
     }
+    // exclusive running maximum of the threads' last counts: where this thread's first run starts
+    int m = last_n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int h = __shfl_up_sync(0xffffffffu, m, o);
+        if (lane >= o) m = max(m, h);
+    }
+    int prev = __shfl_up_sync(0xffffffffu, m, 1);
+    if (lane == 0) prev = -1;
+    if (lane == 31) sm.red_n[warp] = m;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) prev = max(prev, sm.red_n[w]);
+    const int start0 = max(prev, 0);
+    const int32_t base = (int32_t)(t0 + th.e0);
 
-    // ---------------- multinomial: table of tile boundaries, then the draws
-    const int T = p.n_tiles;
-    const double W = sm.W;
-    const double invW = 1.0 / W;
-    __syncthreads();
-    for (int q = tid; q < T; q += kThreads) {
-        const double b = sm.Bs[q] * invW;
-        const float hi = (float)b;
-        sm.u.m.bhi[q] = hi;
-        sm.u.m.blo[q] = (float)(b - (double)hi);
-        sm.u.m.rho[q] = (float)ldexp(W, sm.K - sm.kt[q]);
+    // Run-length decode, one staging chunk at a time: each positive element
+    // marks the first slot of its run [N_{i-1}, N_i) with its index (runs of
+    // later elements start later, so indices increase along the chunk), the
+    // element whose run covers the chunk's first slot marks that slot, and an
+    // inclusive max-scan over the chunk fills every run.  Chunk slot s sits at
+    // out[s + shift] so that out[x] maps to the 16-byte aligned global position
+    // gb + x; each thread scans and stores 16 consecutive entries.
+    int32_t* out = sm.u.s.out;
+    constexpr int kSlots = kIoCap / kThreads;  // entries per thread in the scan
+    constexpr int kChunk = kIoCap - 4;         // offsets per chunk (room for the shift)
+    for (int c0 = 0; c0 < noff; c0 += kChunk) {
+        const int c1 = min(noff, c0 + kChunk);
+        const int shift = (int)((jlo + c0) & 3);
+#pragma unroll
+        for (int q = 0; q < kSlots / 4; ++q)
+            *reinterpret_cast<int4*>(&out[tid * kSlots + 4 * q]) = make_int4(-1, -1, -1, -1);
+        __syncthreads();
+        int a = start0;
+#pragma unroll
+        for (int i = 0; i < kMaxPerThread; ++i) {
+            if (i < th.K && ((th.pos >> i) & 1u)) {
+                const int b = __float_as_int(th.v[i]);
+                if (b > a) {
+                    if (a >= c0 && a < c1) out[a - c0 + shift] = base + i;
+                    else if (a < c0 && b > c0) out[shift] = base + i;
+                }
+                a = b;
+            }
+        }
+        __syncthreads();
+        int4 r[kSlots / 4];
+        int run = -1;
+#pragma unroll
+        for (int q = 0; q < kSlots / 4; ++q) {
+            r[q] = *reinterpret_cast<const int4*>(&out[tid * kSlots + 4 * q]);
+            r[q].x = run = max(run, r[q].x);
+            r[q].y = run = max(run, r[q].y);
+            r[q].z = run = max(run, r[q].z);
+            r[q].w = run = max(run, r[q].w);
+        }
+        int mm = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int h = __shfl_up_sync(0xffffffffu, mm, o);
+            if (lane >= o) mm = max(mm, h);
+        }
+        int carry = __shfl_up_sync(0xffffffffu, mm, 1);
+        if (lane == 0) carry = -1;
+        if (lane == 31) sm.red_n[warp] = mm;
+        __syncthreads();
+        for (int w = 0; w < warp; ++w) carry = max(carry, sm.red_n[w]);
+        // entries x in [tid*kSlots, +kSlots) hold chunk slots x - shift
+        const int x0i = tid * kSlots;
+        const int lo = max(x0i, shift), hi = min(x0i + kSlots, shift + (c1 - c0));
+        if (hi > lo) {
+            int32_t* g = p.anc + (jlo + c0 - shift) + x0i;  // 16-byte aligned
+            int vals[kSlots];
+#pragma unroll
+            for (int q = 0; q < kSlots / 4; ++q) {
+                vals[4 * q + 0] = max(carry, r[q].x);
+                vals[4 * q + 1] = max(carry, r[q].y);
+                vals[4 * q + 2] = max(carry, r[q].z);
+                vals[4 * q + 3] = max(carry, r[q].w);
+            }
+            if (lo == x0i && hi == x0i + kSlots) {
+#pragma unroll
+                for (int q = 0; q < kSlots / 4; ++q)
+                    *reinterpret_cast<int4*>(g + 4 * q) =
+                        make_int4(vals[4 * q], vals[4 * q + 1], vals[4 * q + 2], vals[4 * q + 3]);
+            } else {
+#pragma unroll
+                for (int z = 0; z < kSlots; ++z)
+                    if (x0i + z >= lo && x0i + z < hi) g[z] = vals[z];
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Multinomial draws (Figure 1a): binary searches in global units.
+// ---------------------------------------------------------------------------
+__device__ void multinomial_draws(const SortedParams& p, PersistShared& sm) {
+    const int tid = threadIdx.x, t = blockIdx.x;
+    const int T = p.n_tiles;
+    const float Wh = sm.W_hi, Wl = sm.W_lo;
     const int64_t nq = (p.P + 3) >> 2;  // four draws per Philox block
     const int64_t q_beg = nq * t / T, q_end = nq * (t + 1) / T;
     for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
@@ -326,24 +375,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         for (int s = 0; s < 4; ++s) {
             float uh, ul;
             u32_pair(word_of(r, s), uh, ul);
-            // last tile with B_t / W <= u
+            // target u W as a float pair
+            const float th = __fmul_rn(uh, Wh);
+            const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
+            // last tile whose carry is <= the target (compared by value)
             int lo = 0, hi = T - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                const float bh = sm.u.m.bhi[mid];
-                if (bh < uh || (bh == uh && sm.u.m.blo[mid] <= ul)) lo = mid;
+                const float d = __fadd_rn(__fsub_rn(sm.u.m.bhi[mid], th), __fsub_rn(sm.u.m.blo[mid], tl));
+                if (d <= 0.f) lo = mid;
                 else hi = mid - 1;
             }
-            const int tt = lo;
-            const float du = __fadd_rn(__fsub_rn(uh, sm.u.m.bhi[tt]), __fsub_rn(ul, sm.u.m.blo[tt]));
-            const float tau = fmaxf(0.f, du * sm.u.m.rho[tt]);
+            int tt = lo;
+            while (tt > 0 && sm.il[tt] < 0) --tt;  // never settle on a tile without weight
+            // tile-local target as a pair (exact binary scaling)
+            const float sc = sm.u.m.sc[tt];
+            float xh = __fmul_rn(__fsub_rn(th, sm.u.m.bhi[tt]), sc);
+            float xl = __fmul_rn(__fsub_rn(tl, sm.u.m.blo[tt]), sc);
+            if (xh + xl < 0.f) {
+                xh = 0.f;
+                xl = 0.f;
+            }
             const int64_t b0 = (int64_t)tt * p.tile;
             const int nt = (int)min((int64_t)p.tile, p.P - b0);
             const float* vt = p.v_out + b0;
             int l2 = 0, h2 = nt;
             while (l2 < h2) {
                 const int mid = (l2 + h2) >> 1;
-                if (fabsf(__ldcg(vt + mid)) > tau) h2 = mid;
+                // |v| > xh + xl, with |v| - xh exact near the decision
+                if (__fsub_rn(fabsf(__ldcg(vt + mid)), xh) > xl) h2 = mid;
                 else l2 = mid + 1;
             }
             int idx = sm.il[tt];
@@ -372,6 +432,69 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
 }
 
 template <int KIND>
+__global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int t = blockIdx.x;
+    const uint64_t t_start = global_ns();
+    const uint32_t epoch = ld_relaxed_u32(p.ctl + CTL_EPOCH) + 1u;
+
+    const int64_t t0 = (int64_t)t * p.tile;
+    const int n = (int)min((int64_t)p.tile, p.P - t0);
+
+    TileThread th;
+    const TileSummary ts = tile_scan(p.lw + t0, n, sm.tile, th);
+    if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
+
+    if (KIND == KIND_MULTI) {
+        // the tile's cumulative weights (sign bit: zero weight) for the searches
+        float* vg = p.v_out + t0 + th.e0;
+#pragma unroll
+        for (int q = 0; q < kMaxPerThread / 4; ++q) {
+            if (4 * q < th.K) {
+                float o[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int i = 4 * q + r;
+                    o[r] = ((th.pos >> i) & 1u) ? th.v[i] : -th.v[i];
+                }
+                if (th.e0 + 4 * q + 3 < n) {
+                    *reinterpret_cast<float4*>(vg + 4 * q) = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (th.e0 + 4 * q + r < n) vg[4 * q + r] = o[r];
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+    }
+
+    bool ok = arrive_and_wait(p, sm, ts, epoch, t_start);
+    if (!ok && tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
+    if (ok) ok = carries<KIND>(p, sm, t);
+    // every CTA read the epoch before arriving, and CTA 0 has seen all arrivals
+    // (or waited out its limit): reset the counter the next launch will use and
+    // advance the epoch
+    if (t == 0 && tid == 0) {
+        atomicExch(p.ctl + CTL_ARRIVE0 + ((epoch + 1u) & 1u), 0u);
+        atomicExch(p.ctl + CTL_EPOCH, epoch);
+    }
+    if (!ok) return;
+
+    if (KIND == KIND_MULTI) {
+        __syncthreads();
+        multinomial_draws(p, sm);
+        return;
+    }
+    if (tid == 0) tile_offsets<KIND>(p, sm, ts.k);
+    __syncthreads();
+    assign_offspring<KIND>(p, sm, th, ts, t0);
+}
+
+template <int KIND>
 static cudaError_t set_smem_attr() {
     return cudaFuncSetAttribute(k_persistent<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(PersistShared));
@@ -393,6 +516,7 @@ static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) 
 }
 
 cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s) {
+    if (grid > kMaxTiles) return cudaErrorInvalidValue;
     switch (kind) {
     case KIND_MULTI: return launch_kind<KIND_MULTI>(p, grid, s);
     case KIND_STRAT: return launch_kind<KIND_STRAT>(p, grid, s);

@@ -9,9 +9,9 @@
 //   2. forms w_i = exp(lw_i - k_t ln 2) with an error-free subtraction;
 //   3. runs a Kahan-compensated serial scan per thread and a block scan of the
 //      per-thread totals in float pairs;
-//   4. writes the tile-local inclusive cumulative weights v_i (float, made
-//      monotone across threads) to shared memory.  The sign bit of v_i marks
-//      zero-weight elements, which the searches never return.
+//   4. leaves in registers the tile-local inclusive cumulative weights v_i
+//      (float, made monotone across threads) and a bit mask of the elements
+//      with positive weight.
 #pragma once
 
 #include "pf_device.cuh"
@@ -21,8 +21,7 @@ namespace pf {
 constexpr int kWarps = kThreads / 32;
 
 struct TileShared {
-    float vs[kTileMax];        // v_i, sign bit set for zero weights
-    float Vb[kThreads + 1];    // per-thread bases, monotone
+    float Vb[kThreads + 1];  // per-thread bases, monotone
     float redf[kWarps];
     fpair redp[kWarps];
     fpair total;
@@ -34,6 +33,14 @@ struct TileSummary {
     fpair S;      // tile sum relative to 2^k (compensated pair)
     int i_last;   // tile-local index of the last positive weight, -1 if none
     int bad;      // a NaN or +inf log-weight was seen
+};
+
+// This thread's share of the tile.
+struct TileThread {
+    float v[kMaxPerThread];  // tile-local inclusive cumulative weight of element e0 + i
+    uint32_t pos;            // bit i: element e0 + i has positive weight
+    int K;                   // elements per thread
+    int e0;                  // first tile-local element of this thread
 };
 
 __device__ __forceinline__ int per_thread_count(int n) {
@@ -64,17 +71,20 @@ __device__ __forceinline__ void tile_load(const float* __restrict__ base, int n,
     }
 }
 
-// Block-wide; every thread of the CTA must call it.  Leaves sm.vs[0..n) filled
-// and returns the tile summary (identical in every thread).
-__device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base, int n, TileShared& sm) {
+// Block-wide; every thread of the CTA must call it.  Fills th (this thread's
+// elements) and returns the tile summary (identical in every thread).
+__device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base, int n, TileShared& sm,
+                                                 TileThread& th) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = per_thread_count(n);
     const int e0 = tid * K;
+    th.K = K;
+    th.e0 = e0;
 
     if (tid == 0) sm.i_last = -1;
 
-    float x[kMaxPerThread];
-    tile_load(base, n, e0, K, x);
+    float* x = th.v;
+    tile_load(base, n, e0, K, th.v);
 
     // 1. tile maximum and domain check
     float m = -INFINITY;
@@ -112,6 +122,7 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
             x[i] = s;
         }
     }
+    th.pos = posbits;
 
     // block exclusive scan of the per-thread totals (float pairs)
     const fpair tot = {s, -c};
@@ -151,25 +162,7 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
     // take the next base so that no gap is left between threads
     const float Vk = sm.Vb[tid], Vn = sm.Vb[tid + 1];
 #pragma unroll
-    for (int q = 0; q < kMaxPerThread / 4; ++q) {
-        if (4 * q < K && e0 + 4 * q < n) {
-            float o[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int i = 4 * q + r;
-                float v = (i >= p) ? Vn : fminf(__fadd_rn(Vk, x[i]), Vn);
-                o[r] = ((posbits >> i) & 1u) ? v : -v;
-            }
-            if (e0 + 4 * q + 3 < n) {
-                *reinterpret_cast<float4*>(&sm.vs[e0 + 4 * q]) = make_float4(o[0], o[1], o[2], o[3]);
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (e0 + 4 * q + r < n) sm.vs[e0 + 4 * q + r] = o[r];
-            }
-        }
-    }
-    __syncthreads();
+    for (int i = 0; i < kMaxPerThread; ++i) x[i] = (i >= p) ? Vn : fminf(__fadd_rn(Vk, x[i]), Vn);
 
     TileSummary ts;
     ts.k = k;
@@ -177,13 +170,6 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
     ts.i_last = sm.i_last;
     ts.bad = bad;
     return ts;
-}
-
-// First non-zero-weight element at or after i in vs[0..n); falls back to i_last.
-__device__ __forceinline__ int next_positive(const float* vs, int n, int i, int i_last) {
-    for (int q = i; q < n; ++q)
-        if (!zero_flag(vs[q])) return q;
-    return i_last;
 }
 
 }  // namespace pf

@@ -137,10 +137,15 @@ def test_one_hot_and_equal_weights():
         for kind, (fn, _) in CUMULATIVE.items():
             a, st = gpu_resample(fn, lw, 2)
             assert st == pf.PF_OK and np.all(a == P // 3), kind
+        # equal weights: the oracle gives the identity; the GPU may differ only at
+        # strata whose offset lies within the near-tie band of a stratum edge
         eq = np.full(P, -3.25, np.float32)
         for kind in ("systematic", "stratified"):
             a, st = gpu_resample(CUMULATIVE[kind][0], eq, 4)
-            assert st == pf.PF_OK and np.array_equal(a, np.arange(P)), kind
+            assert st == pf.PF_OK
+            assert np.array_equal(CUMULATIVE[kind][1](eq, 4), np.arange(P))
+            rep = check_cumulative(kind, eq, a, np.arange(P), 4)
+            assert rep.ok and rep.mismatches <= max(2, P // 1000), (kind, rep.summary())
 
 
 def test_extreme_log_weights():
