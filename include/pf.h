@@ -212,6 +212,41 @@ pf_status pf_set_wait_limit_ns(uint64_t ns);
  */
 pf_status pf_debug_skip_publish(int64_t tile);
 
+/* Largest P accepted by pf_resample_multinomial_static. */
+#define PF_STATIC_MAX_PARTICLES (1LL << 20)
+
+/*
+ * Multinomial resampling that allocates nothing.  (The paper has no
+ * counterpart; this is a deployment variant of pf_resample_multinomial.)
+ *
+ * For callers that cannot let a library allocate device memory -- code whose
+ * allocator owns all device memory, real-time loops where a first-call
+ * cudaMalloc (which also synchronises the device) would stall a deadline, or
+ * programs that forbid allocation after start-up.  It computes exactly what
+ * pf_resample_multinomial computes (same kernel, same random streams) but
+ * keeps its scratch in a fixed array compiled into the library: about 4 MiB
+ * of device memory (PF_STATIC_MAX_PARTICLES floats plus 16 KiB of control
+ * data), present on every GPU that loads the library until the process exits.
+ *   logw          [P] float, device, 16-byte aligned               (in)
+ *   P             1 <= P <= PF_STATIC_MAX_PARTICLES; larger P returns
+ *                 PF_ERR_INVALID without doing anything
+ *   seed          Philox key
+ *   ancestors     [P] int32, device, 16-byte aligned               (out)
+ *   device_status [1] uint32, device, or NULL: receives this call's
+ *                 device-side status (0 = ok, else a pf_status code)  (out)
+ * No cudaMalloc, cudaFree or other allocating call is made.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * and the kernel's launch limits; make that first call before capturing any
+ * stream into a CUDA graph.  Every call on every stream shares the one array
+ * and it keeps the previous call's contents, so calls that may overlap on the
+ * GPU (different streams without ordering between them) race and give wrong
+ * results: order them, or use pf_resample_multinomial, whose scratch is per
+ * stream.  pf_get_device_status does not see this call's errors; use
+ * device_status.
+ */
+pf_status pf_resample_multinomial_static(const float* logw, int64_t P, uint64_t seed, int32_t* ancestors,
+                                         uint32_t* device_status, void* stream);
+
 /* Library version, major*10000 + minor*100 + patch. */
 int pf_version(void);
 

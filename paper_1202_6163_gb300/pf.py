@@ -37,6 +37,7 @@ SIGNATURES = {
     "pf_set_wait_limit_ns": (_INT, [_U64]),
     "pf_debug_skip_publish": (_INT, [_I64]),
     "pf_version": (_INT, []),
+    "pf_resample_multinomial_static": (_INT, [_VP, _I64, _U64, _VP, _VP, _VP]),
 }
 
 
@@ -144,6 +145,12 @@ def pf_set_wait_limit_ns(ns: int):
 
 def pf_debug_skip_publish(tile: int):
     _check(load().pf_debug_skip_publish(tile), "pf_debug_skip_publish")
+
+
+def pf_resample_multinomial_static(logw, P, seed, ancestors, device_status=None, stream=None):
+    """Multinomial resampling with the library's fixed scratch array (no allocation)."""
+    _check(load().pf_resample_multinomial_static(_ptr(logw), P, seed, _ptr(ancestors), _ptr(device_status),
+                                                 _stream(stream)), "pf_resample_multinomial_static")
 
 
 def pf_version() -> int:
