@@ -29,7 +29,7 @@ using namespace pf;
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kMaxPersistTiles = 1024;
+constexpr int kMaxRecords = kMaxTilesTotal;  // 16-byte tile records per workspace
 constexpr uint32_t kMetroBCap = 1u << 24;
 
 struct DeviceInfo {
@@ -40,7 +40,7 @@ struct DeviceInfo {
 
 struct Workspace {
     uint32_t* ctl = nullptr;     // CTL_WORDS control words
-    uint64_t* slots = nullptr;   // 4 words per tile of the single-launch kernels
+    uint64_t* slots = nullptr;   // one 16-byte record per tile of the single-launch kernels
     void* scratch = nullptr;     // per-call scratch (multinomial cumulative weights, reduction records)
     size_t scratch_bytes = 0;
 };
@@ -88,10 +88,10 @@ pf_status workspace(cudaStream_t s, size_t scratch, Workspace*& out) {
         if (capturing(s)) return PF_ERR_NOMEM;
         e = cudaMalloc(&w.ctl, CTL_WORDS * sizeof(uint32_t));
         if (e != cudaSuccess) return PF_ERR_NOMEM;
-        e = cudaMalloc(&w.slots, 4 * kMaxPersistTiles * sizeof(uint64_t));
+        e = cudaMalloc(&w.slots, 2 * kMaxRecords * sizeof(uint64_t));
         if (e != cudaSuccess) return PF_ERR_NOMEM;
         e = cudaMemsetAsync(w.ctl, 0, CTL_WORDS * sizeof(uint32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.slots, 0, 4 * kMaxPersistTiles * sizeof(uint64_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.slots, 0, 2 * kMaxRecords * sizeof(uint64_t), s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     }
     if (scratch > w.scratch_bytes) {
@@ -115,25 +115,34 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 size_t reduce_scratch(int64_t P) { return (size_t)reduce_tiles(P) * reduce_record_bytes(); }
 
-// Tile layout of a single-launch call: grid G <= G_max tiles of `tile` elements
-// (a multiple of 4), at least ~2K elements per tile.
-bool persistent_layout(int64_t P, int G_max, int& G, int& tile) {
+// Tile layout of a single-launch call: T tiles of `tile` log-weights (a
+// multiple of 4, at most kTileMax), R consecutive tiles per CTA, G <= G_max
+// resident CTAs.  While P fits one tile per resident CTA, tiles hold at least
+// ~2K log-weights and R = 1; beyond that tiles are full and R grows.
+bool persistent_layout(int64_t P, int G_max, int& G, int& tile, int& T, int& R) {
     if (G_max < 1) return false;
-    if (G_max > kMaxPersistTiles) G_max = kMaxPersistTiles;
-    if (P > (int64_t)G_max * kTileMax) return false;
-    const char* env = std::getenv("PF_MIN_TILE");
-    int64_t min_tile = env ? std::atoll(env) : 2048;
-    if (min_tile < 4) min_tile = 4;
-    int64_t g = (P + min_tile - 1) / min_tile;
-    if (g > G_max) g = G_max;
-    if (g < 1) g = 1;
-    int64_t t = (P + g - 1) / g;
-    t = (t + 3) & ~int64_t(3);
-    if (t > kTileMax) t = kTileMax;
-    g = (P + t - 1) / t;
-    G = (int)g;
-    tile = (int)t;
-    return G <= G_max;
+    if (P > (int64_t)kMaxTilesTotal * kTileMax) return false;
+    if (P <= (int64_t)G_max * kTileMax) {
+        const char* env = std::getenv("PF_MIN_TILE");
+        int64_t min_tile = env ? std::atoll(env) : 2048;
+        if (min_tile < 4) min_tile = 4;
+        int64_t g = (P + min_tile - 1) / min_tile;
+        if (g > G_max) g = G_max;
+        if (g < 1) g = 1;
+        int64_t t = (P + g - 1) / g;
+        t = (t + 3) & ~int64_t(3);
+        if (t > kTileMax) t = kTileMax;
+        T = (int)((P + t - 1) / t);
+        tile = (int)t;
+        G = T;
+        R = 1;
+        return true;
+    }
+    tile = kTileMax;
+    T = (int)((P + kTileMax - 1) / kTileMax);
+    R = (T + G_max - 1) / G_max;
+    G = (T + R - 1) / R;
+    return R <= 64;
 }
 
 pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t seed, int32_t* anc, void* stream) {
@@ -145,9 +154,9 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     DeviceInfo* info;
     pf_status st = device_info(dev, info);
     if (st) return st;
-    int G, tile;
-    if (!persistent_layout(P, info->num_sms * info->persist_per_sm[kind], G, tile)) {
-        return PF_ERR_INVALID;  // larger P: multi-pass path
+    int G, tile, T, R;
+    if (!persistent_layout(P, info->num_sms * info->persist_per_sm[kind], G, tile, T, R)) {
+        return PF_ERR_INVALID;  // P beyond kMaxTilesTotal full tiles
     }
     Workspace* w;
     st = workspace(s, kind == PF_MULTINOMIAL ? (size_t)P * sizeof(float) : 0, w);
@@ -158,7 +167,8 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     p.P = P;
     p.Pd = (double)P;
     p.tile = tile;
-    p.n_tiles = G;
+    p.n_tiles = T;
+    p.tiles_per_cta = R;
     p.key0 = (uint32_t)(seed & 0xffffffffu);
     p.key1 = (uint32_t)(seed >> 32);
     p.filter = 0;

@@ -34,6 +34,7 @@ enum : int {
 constexpr int kThreads = 512;     // threads per CTA of the tile kernels
 constexpr int kMaxPerThread = 16; // elements per thread (multiple of 4)
 constexpr int kTileMax = kThreads * kMaxPerThread;
+constexpr int kMaxTilesTotal = 4096;  // tiles of one single-launch call (P <= 2^25)
 
 // Per-tile record of the multi-pass scan (decoupled lookback).
 struct TileRecord {
@@ -51,10 +52,11 @@ struct SortedParams {
     int64_t P;
     double Pd;     // P as a double
     int tile;      // elements per tile (multiple of 4, <= kTileMax)
-    int n_tiles;   // tiles (CTAs) of the launch
+    int n_tiles;   // tiles of the launch (T)
+    int tiles_per_cta;  // consecutive tiles owned by each CTA (R >= 1; 0 means 1)
     uint32_t key0, key1, filter;
     uint32_t* ctl;
-    uint64_t* slots;  // 3 words per tile
+    uint64_t* slots;  // one 16-byte record per tile
     uint64_t wait_ns;
     int skip_tile;
     float* v_out;     // multinomial: tile-local cumulative weights (P floats), else null

@@ -1,26 +1,28 @@
 // Single-launch resamplers for the cumulative schemes (Figure 1a-c).
 //
-// One cooperative launch, one tile per CTA, every CTA resident:
-//   1. tile scan (pf_tile.cuh): the tile's weights and, in registers, its
-//      local cumulative weights v_i; its sum S_t relative to 2^{k_t};
-//   2. publish (k_t, S_t, i_last) and arrive on an epoch's counter; one thread
-//      per CTA waits (bounded) until every tile has arrived;
-//   3. every CTA reads all tiles' words and forms the inter-tile carries
+// One cooperative launch; every CTA is resident and owns R >= 1 consecutive
+// tiles of log-weights:
+//   1. pass 1, per owned tile: tile scan (pf_tile.cuh) -- the tile's weights,
+//      its local cumulative weights v_i, its sum S_t relative to 2^{k_t} --
+//      and a 16-byte record (k_t, S_t, i_last) in global memory;
+//   2. the CTA arrives on this launch's counter (release) and one thread waits,
+//      with a time limit, until every CTA has arrived;
+//   3. every CTA reads all T records and forms the inter-tile carries
 //          B_t = sum_{t' < t} S_t' 2^{k_t' - K}
 //      as exact 128-bit fixed-point sums (2^-90 resolution relative to the
 //      largest tile reference 2^K).  Integer sums are exact and associative, so
 //      every CTA holds bit-identical boundaries, and W = B_T is the scan's own
 //      last prefix;
 //   4. systematic / stratified (Section 2: these schemes yield offspring
-//      counts): the tile owns the offsets j whose position (j + u_j) W / P lies
-//      in [B_t, B_{t+1}); each element counts the offsets below its cumulative
-//      weight, N_i, and its ancestor index fills [N_{i-1}, N_i): a run-length
-//      decode in shared memory (mark run starts, then a block max-scan), with
-//      no per-thread loops over run lengths, stored with 128-bit writes;
-//      multinomial: the tile's v_i were written to global memory before
-//      arriving; the CTA draws a balanced slice of the P uniforms, finds the
-//      tile by binary search over the boundaries and the element by binary
-//      search in that tile's v_i.
+//      counts), per owned tile (re-scanned when R > 1): the tile owns the
+//      offsets j whose position (j + u_j) W / P lies in [B_t, B_{t+1}); each
+//      element counts the offsets below its cumulative weight, N_i, and its
+//      index fills [N_{i-1}, N_i) by a run-length decode in shared memory (mark
+//      run starts, block max-scan), stored with 128-bit writes;
+//      multinomial: the tiles' v_i were written to global memory in pass 1;
+//      the CTA draws a balanced slice of the P uniforms, finds the tile by a
+//      binary search over the boundaries and the element by a binary search in
+//      that tile's v_i.
 // Every global write is bounded by [0, P) whatever the data; a NaN/+inf or
 // all-zero weight set records PF_ERR_DOMAIN and writes no ancestors.
 #include <climits>
@@ -30,51 +32,47 @@
 
 namespace pf {
 
-constexpr int kMaxTiles = 2 * kThreads;  // two tiles read per thread
-constexpr int kIoCap = 8192;             // offsets per staging chunk
-
+constexpr int kMaxOwn = 64;    // tiles per CTA
+constexpr int kIoCap = 8192;   // staging entries of the run-length decode
 enum { KIND_MULTI = 0, KIND_STRAT = 1, KIND_SYS = 2 };
+
+struct TableEntry {  // multinomial: one tile's lower boundary and scale
+    float bhi, blo;  // B_t as a float pair (units of 2^K)
+    float sc;        // 2^(K - k_t): global units -> tile-local units
+    int il;          // last positive element of the tile, -1 if none
+};
 
 struct PersistShared {
     TileShared tile;
-    union {
-        struct {
-            int32_t out[kIoCap];
-        } s;
-        struct {
-            float bhi[kMaxTiles], blo[kMaxTiles], sc[kMaxTiles];
-        } m;
-    } u;
-    int il[kMaxTiles];
     i128 wsum[kWarps];
-    i128 Bl, Bh, Wt;
+    i128 Wt;
+    i128 Bown[kMaxOwn + 1];  // boundaries of this CTA's tiles (systematic, stratified)
     int red_k[kWarps];
     int red_n[kWarps];
-    int noff, K, ok;
+    int noff, K, ok, pad;
     long long jlo;
     float tau0, inv_rho, W_hi, W_lo;
 };
+// Dynamic shared memory: PersistShared, then either the staging buffer
+// int32 out[kIoCap] (systematic, stratified) or TableEntry table[T] (multinomial).
 
+__host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T) {
+    return sizeof(PersistShared) + (kind == KIND_MULTI ? (size_t)T * sizeof(TableEntry) : kIoCap * sizeof(int32_t));
+}
 
 // ---------------------------------------------------------------------------
 // Arrival and carries.  Block-wide; identical results in every CTA.
 // ---------------------------------------------------------------------------
-// Publish the tile's 16-byte record (k, S_hi, S_lo, i_last), arrive on this
-// epoch's counter with release semantics, and wait (one thread, bounded)
-// until every tile has arrived.
-__device__ bool arrive_and_wait(const SortedParams& p, PersistShared& sm, const TileSummary& ts, uint32_t epoch,
+// Arrive on this epoch's counter with release semantics (after the CTA's
+// records are written) and wait, one thread, bounded, for every CTA.
+__device__ bool arrive_and_wait(const SortedParams& p, PersistShared& sm, bool skip, uint32_t epoch,
                                 uint64_t t_start) {
     const int tid = threadIdx.x;
-    const int t = blockIdx.x;
     uint32_t* arrive = p.ctl + CTL_ARRIVE0 + (epoch & 1u);
     if (tid == 0) {
-        if (t != p.skip_tile) {
-            st_v4_u32(reinterpret_cast<uint32_t*>(p.slots) + 4 * t, (uint32_t)ts.k,
-                      __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo), (uint32_t)ts.i_last);
-            red_release_add_u32(arrive, 1u);
-        }
+        if (!skip) red_release_add_u32(arrive, 1u);
         int ok = 1;
-        for (uint32_t it = 1; ld_acquire_u32(arrive) < (uint32_t)p.n_tiles; ++it) {
+        for (uint32_t it = 1; ld_acquire_u32(arrive) < gridDim.x; ++it) {
             if ((it & 7u) == 0u && global_ns() - t_start > p.wait_ns) {
                 ok = 0;
                 break;
@@ -105,26 +103,17 @@ __device__ __forceinline__ i128 block_scan_i128(PersistShared& sm, i128 x) {
 }
 
 template <int KIND>
-__device__ bool carries(const SortedParams& p, PersistShared& sm, int my_tile) {
+__device__ bool carries(const SortedParams& p, PersistShared& sm, TableEntry* table, int t_first, int t_count) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = p.n_tiles;
-    const uint32_t* slots = reinterpret_cast<const uint32_t*>(p.slots);
-    // thread tid owns tiles tid and tid + kThreads; coalesced 16-byte reads
-    uint4 r[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-        if (tid + q * kThreads < T) r[q] = ld_cg_v4_u32(slots + 4 * (tid + q * kThreads));
+    const uint32_t* rec = reinterpret_cast<const uint32_t*>(p.slots);
+    // largest tile exponent among tiles with weight; NaN/+inf check
     int bad = 0, kmax = INT_MIN;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        if (tid + q * kThreads < T) {
-            const float sh = __uint_as_float(r[q].y);
-            bad |= !(sh <= 3.402823466e38f);  // a tile saw NaN/+inf
-            if (sh > 0.f) kmax = max(kmax, (int)r[q].x);
-        } else {
-            r[q].y = 0u;
-            r[q].z = 0u;
-        }
+    for (int t = tid; t < T; t += kThreads) {
+        const uint4 r = ld_cg_v4_u32(rec + 4 * t);
+        const float sh = __uint_as_float(r.y);
+        bad |= !(sh <= 3.402823466e38f);
+        if (sh > 0.f) kmax = max(kmax, (int)r.x);
     }
     kmax = warp_max_i(kmax);
     if (lane == 0) sm.red_k[warp] = kmax;
@@ -136,33 +125,31 @@ __device__ bool carries(const SortedParams& p, PersistShared& sm, int my_tile) {
         if (tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
         return false;
     }
-    i128 base = 0;
-    for (int q = 0; q < 2 && q * kThreads < T; ++q) {
-        const int t = tid + q * kThreads;
-        const int sh = (int)r[q].x - K;
-        const i128 a = fixed_of(__uint_as_float(r[q].y), sh) + fixed_of(__uint_as_float(r[q].z), sh);
-        const i128 B = base + block_scan_i128(sm, a);  // carry of tile t
-        const i128 total = base + sm.Wt;
+    // exact prefix sums of the tile masses, kThreads tiles per pass
+    i128 running = 0;
+    for (int base = 0; base < T; base += kThreads) {
+        const int t = base + tid;
+        uint4 r = make_uint4(0, 0, 0, 0xffffffffu);
+        if (t < T) r = ld_cg_v4_u32(rec + 4 * t);
+        const int sh = (int)r.x - K;
+        const i128 a = (t < T) ? fixed_of(__uint_as_float(r.y), sh) + fixed_of(__uint_as_float(r.z), sh) : (i128)0;
+        const i128 B = running + block_scan_i128(sm, a);  // carry of tile t
+        running += sm.Wt;
         __syncthreads();  // sm.wsum / sm.Wt are reused by the next pass
         if (t < T) {
             if (KIND == KIND_MULTI) {
                 const fpair b = fixed_to_pair(B);
-                sm.u.m.bhi[t] = b.hi;
-                sm.u.m.blo[t] = b.lo;
-                sm.u.m.sc[t] = pow2f(-sh);
-                sm.il[t] = (int)r[q].w;
-            } else {
-                if (t == my_tile) sm.Bl = B;
-                if (t == my_tile + 1) sm.Bh = B;
+                table[t] = {b.hi, b.lo, pow2f(-sh), (int)r.w};
+            } else if (t >= t_first && t <= t_first + t_count) {
+                sm.Bown[t - t_first] = B;
             }
         }
-        base = total;
     }
     if (tid == 0) {
         sm.K = K;
-        sm.Wt = base;
-        if (KIND != KIND_MULTI && my_tile + 1 == T) sm.Bh = base;
-        const fpair Wp = fixed_to_pair(base);
+        sm.Wt = running;
+        if (KIND != KIND_MULTI && t_first + t_count == T) sm.Bown[t_count] = running;
+        const fpair Wp = fixed_to_pair(running);
         sm.W_hi = Wp.hi;
         sm.W_lo = Wp.lo;
     }
@@ -175,27 +162,27 @@ __device__ bool carries(const SortedParams& p, PersistShared& sm, int my_tile) {
 // ---------------------------------------------------------------------------
 // Per-tile scalars (thread 0), in float pairs: the tile's offset range and the
 // map from tile-local cumulative weight v to the offset coordinate
-// y = v * inv_rho + x0 (offsets counted from jlo).  P < 2^24 on this path.
+// y = v * inv_rho + x0 (offsets counted from jlo).  P <= 2^25 on this path.
 template <int KIND>
-__device__ void tile_offsets(const SortedParams& p, PersistShared& sm, int k_tile) {
+__device__ void tile_offsets(const SortedParams& p, PersistShared& sm, i128 Bl_i, i128 Bh_i, int k_tile) {
     const fpair W = {sm.W_hi, sm.W_lo};
-    const fpair Bl = fixed_to_pair(sm.Bl), Bh = fixed_to_pair(sm.Bh);
-    const float Ph = (float)p.P;  // exact: P < 2^24
-    const fpair PW = pair_div({Ph, 0.f}, W);
+    const fpair Bl = fixed_to_pair(Bl_i), Bh = fixed_to_pair(Bh_i);
+    const fpair Pp = fast_two_sum((float)p.P, (float)(p.P - (int64_t)(float)p.P));  // P exactly
+    const fpair PW = pair_div(Pp, W);
     const fpair yl = pair_mul(Bl, PW), yh = pair_mul(Bh, PW);  // B P / W
-    const bool last = sm.Bh >= sm.Wt;
+    const bool last = Bh_i >= sm.Wt;
     long long jl, jh;
     float x0;
     if (KIND == KIND_SYS) {
         const u32x4 r = philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1);
         const float u = u23f(r.x);
         const fpair dl = pair_sub_f(yl, u), dh = pair_sub_f(yh, u);
-        jl = (sm.Bl > 0) ? max(0LL, min((long long)p.P, pair_ceil(dl))) : 0;
+        jl = (Bl_i > 0) ? max(0LL, min((long long)p.P, pair_ceil(dl))) : 0;
         jh = last ? p.P : max(0LL, min((long long)p.P, pair_ceil(dh)));
         x0 = __fadd_rn(__fsub_rn(dl.hi, (float)jl), dl.lo);  // N(v) = ceil(v * inv_rho + x0)
     } else {
         jl = 0;
-        if (sm.Bl > 0) {
+        if (Bl_i > 0) {
             const long long f = pair_floor(yl);
             if (f >= p.P) {
                 jl = p.P;
@@ -223,8 +210,8 @@ __device__ void tile_offsets(const SortedParams& p, PersistShared& sm, int k_til
 }
 
 template <int KIND>
-__device__ void assign_offspring(const SortedParams& p, PersistShared& sm, TileThread& th, const TileSummary& ts,
-                                 int64_t t0) {
+__device__ void assign_offspring(const SortedParams& p, PersistShared& sm, int32_t* out, TileThread& th,
+                                 const TileSummary& ts, int64_t t0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int noff = sm.noff;
     const long long jlo = sm.jlo;
@@ -287,7 +274,6 @@ __device__ void assign_offspring(const SortedParams& p, PersistShared& sm, TileT
     // inclusive max-scan over the chunk fills every run.  Chunk slot s sits at
     // out[s + shift] so that out[x] maps to the 16-byte aligned global position
     // gb + x; each thread scans and stores 16 consecutive entries.
-    int32_t* out = sm.u.s.out;
     constexpr int kSlots = kIoCap / kThreads;  // entries per thread in the scan
     constexpr int kChunk = kIoCap - 4;         // offsets per chunk (room for the shift)
     for (int c0 = 0; c0 < noff; c0 += kChunk) {
@@ -362,12 +348,12 @@ __device__ void assign_offspring(const SortedParams& p, PersistShared& sm, TileT
 // ---------------------------------------------------------------------------
 // Multinomial draws (Figure 1a): binary searches in global units.
 // ---------------------------------------------------------------------------
-__device__ void multinomial_draws(const SortedParams& p, PersistShared& sm) {
-    const int tid = threadIdx.x, t = blockIdx.x;
+__device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, const TableEntry* table) {
+    const int tid = threadIdx.x, cta = blockIdx.x, G = gridDim.x;
     const int T = p.n_tiles;
     const float Wh = sm.W_hi, Wl = sm.W_lo;
     const int64_t nq = (p.P + 3) >> 2;  // four draws per Philox block
-    const int64_t q_beg = nq * t / T, q_end = nq * (t + 1) / T;
+    const int64_t q_beg = nq * cta / G, q_end = nq * (cta + 1) / G;
     for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
         const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
         int32_t a[4];
@@ -382,16 +368,16 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm) {
             int lo = 0, hi = T - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                const float d = __fadd_rn(__fsub_rn(sm.u.m.bhi[mid], th), __fsub_rn(sm.u.m.blo[mid], tl));
+                const float d = __fadd_rn(__fsub_rn(table[mid].bhi, th), __fsub_rn(table[mid].blo, tl));
                 if (d <= 0.f) lo = mid;
                 else hi = mid - 1;
             }
             int tt = lo;
-            while (tt > 0 && sm.il[tt] < 0) --tt;  // never settle on a tile without weight
+            while (tt > 0 && table[tt].il < 0) --tt;  // never settle on a tile without weight
+            const TableEntry e = table[tt];
             // tile-local target as a pair (exact binary scaling)
-            const float sc = sm.u.m.sc[tt];
-            float xh = __fmul_rn(__fsub_rn(th, sm.u.m.bhi[tt]), sc);
-            float xl = __fmul_rn(__fsub_rn(tl, sm.u.m.blo[tt]), sc);
+            float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
+            float xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
             if (xh + xl < 0.f) {
                 xh = 0.f;
                 xl = 0.f;
@@ -406,11 +392,11 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm) {
                 if (__fsub_rn(fabsf(__ldcg(vt + mid)), xh) > xl) h2 = mid;
                 else l2 = mid + 1;
             }
-            int idx = sm.il[tt];
+            int idx = e.il;
             if (l2 < nt) {
                 idx = l2;
                 if (zero_flag(__ldcg(vt + idx))) {
-                    int f = sm.il[tt];
+                    int f = e.il;
                     for (int z = idx + 1; z < nt; ++z)
                         if (!zero_flag(__ldcg(vt + z))) {
                             f = z;
@@ -431,73 +417,98 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm) {
     }
 }
 
+// The tile's cumulative weights to global memory (sign bit: zero weight), for the searches.
+__device__ __forceinline__ void write_tile_v(const SortedParams& p, const TileThread& th, int64_t t0, int n) {
+    float* vg = p.v_out + t0 + th.e0;
+#pragma unroll
+    for (int q = 0; q < kMaxPerThread / 4; ++q) {
+        if (4 * q < th.K) {
+            float o[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = 4 * q + r;
+                o[r] = ((th.pos >> i) & 1u) ? th.v[i] : -th.v[i];
+            }
+            if (th.e0 + 4 * q + 3 < n) {
+                *reinterpret_cast<float4*>(vg + 4 * q) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (th.e0 + 4 * q + r < n) vg[4 * q + r] = o[r];
+            }
+        }
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
+    unsigned char* region = smem_raw + sizeof(PersistShared);
     const int tid = threadIdx.x;
-    const int t = blockIdx.x;
     const uint64_t t_start = global_ns();
     const uint32_t epoch = ld_relaxed_u32(p.ctl + CTL_EPOCH) + 1u;
+    const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
+    const int t_first = blockIdx.x * R;
+    const int t_count = max(0, min(R, p.n_tiles - t_first));
+    uint32_t* rec = reinterpret_cast<uint32_t*>(p.slots);
 
-    const int64_t t0 = (int64_t)t * p.tile;
-    const int n = (int)min((int64_t)p.tile, p.P - t0);
-
+    // pass 1: scan and record every owned tile
     TileThread th;
-    const TileSummary ts = tile_scan(p.lw + t0, n, sm.tile, th);
-    if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
-
-    if (KIND == KIND_MULTI) {
-        // the tile's cumulative weights (sign bit: zero weight) for the searches
-        float* vg = p.v_out + t0 + th.e0;
-#pragma unroll
-        for (int q = 0; q < kMaxPerThread / 4; ++q) {
-            if (4 * q < th.K) {
-                float o[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int i = 4 * q + r;
-                    o[r] = ((th.pos >> i) & 1u) ? th.v[i] : -th.v[i];
-                }
-                if (th.e0 + 4 * q + 3 < n) {
-                    *reinterpret_cast<float4*>(vg + 4 * q) = make_float4(o[0], o[1], o[2], o[3]);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        if (th.e0 + 4 * q + r < n) vg[4 * q + r] = o[r];
-                }
-            }
+    TileSummary ts;
+    ts.k = 0;
+    ts.i_last = -1;
+    bool skip = false;
+    for (int r = 0; r < t_count; ++r) {
+        const int t = t_first + r;
+        const int64_t t0 = (int64_t)t * p.tile;
+        const int n = (int)min((int64_t)p.tile, p.P - t0);
+        ts = tile_scan(p.lw + t0, n, sm.tile, th);
+        if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
+        if (KIND == KIND_MULTI) {
+            write_tile_v(p, th, t0, n);
+            __threadfence();
         }
-        __threadfence();
+        if (tid == 0) {
+            skip |= (t == p.skip_tile);
+            st_v4_u32(rec + 4 * t, (uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo),
+                      (uint32_t)ts.i_last);
+        }
         __syncthreads();
     }
 
-    bool ok = arrive_and_wait(p, sm, ts, epoch, t_start);
+    bool ok = arrive_and_wait(p, sm, skip, epoch, t_start);
     if (!ok && tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
-    if (ok) ok = carries<KIND>(p, sm, t);
+    if (ok) ok = carries<KIND>(p, sm, reinterpret_cast<TableEntry*>(region), t_first, t_count);
     // every CTA read the epoch before arriving, and CTA 0 has seen all arrivals
     // (or waited out its limit): reset the counter the next launch will use and
     // advance the epoch
-    if (t == 0 && tid == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
         atomicExch(p.ctl + CTL_ARRIVE0 + ((epoch + 1u) & 1u), 0u);
         atomicExch(p.ctl + CTL_EPOCH, epoch);
     }
     if (!ok) return;
 
     if (KIND == KIND_MULTI) {
-        __syncthreads();
-        multinomial_draws(p, sm);
+        multinomial_draws(p, sm, reinterpret_cast<const TableEntry*>(region));
         return;
     }
-    if (tid == 0) tile_offsets<KIND>(p, sm, ts.k);
-    __syncthreads();
-    assign_offspring<KIND>(p, sm, th, ts, t0);
+    // pass 2: offsets of every owned tile (the last tile's scan is still in registers)
+    int32_t* out = reinterpret_cast<int32_t*>(region);
+    for (int r = t_count - 1; r >= 0; --r) {
+        const int t = t_first + r;
+        const int64_t t0 = (int64_t)t * p.tile;
+        if (r != t_count - 1) ts = tile_scan(p.lw + t0, (int)min((int64_t)p.tile, p.P - t0), sm.tile, th);
+        if (tid == 0) tile_offsets<KIND>(p, sm, sm.Bown[r], sm.Bown[r + 1], ts.k);
+        __syncthreads();
+        assign_offspring<KIND>(p, sm, out, th, ts, t0);
+    }
 }
 
 template <int KIND>
 static cudaError_t set_smem_attr() {
     return cudaFuncSetAttribute(k_persistent<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(PersistShared));
+                                (int)persistent_smem_bytes(KIND, kMaxTilesTotal));
 }
 
 template <int KIND>
@@ -505,7 +516,7 @@ static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = sizeof(PersistShared);
+    cfg.dynamicSmemBytes = persistent_smem_bytes(KIND, p.n_tiles);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -516,7 +527,9 @@ static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) 
 }
 
 cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s) {
-    if (grid > kMaxTiles) return cudaErrorInvalidValue;
+    const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
+    if (p.n_tiles < 1 || p.n_tiles > kMaxTilesTotal || R > kMaxOwn || (int64_t)grid * R < p.n_tiles)
+        return cudaErrorInvalidValue;
     switch (kind) {
     case KIND_MULTI: return launch_kind<KIND_MULTI>(p, grid, s);
     case KIND_STRAT: return launch_kind<KIND_STRAT>(p, grid, s);
@@ -526,11 +539,12 @@ cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, 
 }
 
 // Called once per device: raises the dynamic shared memory limit and returns
-// how many CTAs of the kind fit on one SM (the cooperative grid limit).
+// how many CTAs of the kind fit on one SM (the cooperative grid limit), at the
+// largest shared-memory size a launch may ask for.
 int persistent_blocks_per_sm(int kind) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    const size_t smem = sizeof(PersistShared);
+    const size_t smem = persistent_smem_bytes(kind, kMaxTilesTotal);
     switch (kind) {
     case KIND_MULTI:
         if (set_smem_attr<KIND_MULTI>() == cudaSuccess)

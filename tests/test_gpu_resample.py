@@ -285,3 +285,30 @@ def test_metropolis_autotuned_B():
     assert B in matches or matches, (B, matches)
     assert check_metropolis(lw, B, gpu_resample(pf.pf_resample_metropolis, lw, 3, B)[0],
                             oracle.metropolis(lw, B, 3), 3).ok
+
+
+# ------------------------------------------------------------------ several tiles per CTA (large P)
+@pytest.mark.parametrize("kind", list(CUMULATIVE))
+def test_cumulative_multi_tile_2_6M(kind):
+    P = 2_600_007  # more tiles than resident CTAs
+    lw = workloads.gaussian_logw(P, 1.5, seed=77)
+    rep = assert_cumulative(kind, lw, seed=5)
+    print(kind, "2.6M", rep.summary())
+
+
+@pytest.mark.parametrize("kind", list(CUMULATIVE))
+def test_cumulative_P2e24_heavy_tail(kind):
+    # log-weights N(0,1) with 1% of entries shifted by +10
+    P = 1 << 24
+    lw = workloads.heavy_tail_logw(P, shift=10.0, frac=0.01, seed=3)
+    rep = assert_cumulative(kind, lw, seed=9)
+    print(kind, "2^24", rep.summary())
+
+
+def test_cumulative_beyond_single_launch_capacity_is_rejected():
+    P = (1 << 25) + 1
+    t = torch.zeros(P, device="cuda")
+    a = torch.zeros(P, dtype=torch.int32, device="cuda")
+    with pytest.raises(pf.PFError) as ei:
+        pf.pf_resample_systematic(t, P, 0, 0, a)
+    assert ei.value.status == pf.PF_ERR_INVALID
