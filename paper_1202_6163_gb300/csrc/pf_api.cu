@@ -36,6 +36,7 @@ struct DeviceInfo {
     bool ready = false;
     int num_sms = 0;
     int persist_per_sm[3] = {0, 0, 0};
+    int batched_per_sm[4] = {0, 0, 0, 0};
 };
 
 struct Workspace {
@@ -66,6 +67,8 @@ pf_status device_info(int& dev, DeviceInfo*& info) {
     e = cudaDeviceGetAttribute(&info->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     for (int k = 0; k < 3; ++k) info->persist_per_sm[k] = persistent_blocks_per_sm(k);
+    for (int k = 0; k < 3; ++k) info->batched_per_sm[k] = batched_blocks_per_sm(k);
+    info->batched_per_sm[PF_METROPOLIS] = batched_metropolis_blocks_per_sm();
     e = prepare_metropolis();
     if (e != cudaSuccess) return cuda_fail(e, "prepare_metropolis");
     info->ready = true;
@@ -147,7 +150,10 @@ bool persistent_layout(int64_t P, int G_max, int& G, int& tile, int& T, int& R) 
 
 pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t seed, int32_t* anc, void* stream) {
     if (!logw || !anc || P < 1 || P > PF_MAX_PARTICLES) return PF_ERR_INVALID;
-    if (!aligned16(logw) || !aligned16(anc)) return PF_ERR_INVALID;
+    if (((uintptr_t)logw & 3u) || ((uintptr_t)anc & 3u)) return PF_ERR_INVALID;
+    // tiles are laid out on the 16-byte aligned window that starts `lead` floats before logw
+    const int lead = (int)(((uintptr_t)logw >> 2) & 3u);
+    const int64_t PA = P + lead;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
@@ -155,15 +161,16 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     pf_status st = device_info(dev, info);
     if (st) return st;
     int G, tile, T, R;
-    if (!persistent_layout(P, info->num_sms * info->persist_per_sm[kind], G, tile, T, R)) {
+    if (!persistent_layout(PA, info->num_sms * info->persist_per_sm[kind], G, tile, T, R)) {
         return PF_ERR_INVALID;  // P beyond kMaxTilesTotal full tiles
     }
     Workspace* w;
-    st = workspace(s, kind == PF_MULTINOMIAL ? (size_t)P * sizeof(float) : 0, w);
+    st = workspace(s, kind == PF_MULTINOMIAL ? (size_t)PA * sizeof(float) : 0, w);
     if (st) return st;
     SortedParams p;
-    p.lw = logw;
+    p.lw = logw - lead;
     p.anc = anc;
+    p.lead = lead;
     p.P = P;
     p.Pd = (double)P;
     p.tile = tile;
@@ -268,15 +275,36 @@ pf_status pf_ess(const float* logw, int64_t P, float* ess_out, double* log_sum_o
 
 pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B,
                               const uint64_t* seeds, int32_t* ancestors, void* stream) {
-    (void)kind;
-    (void)logw;
-    (void)offsets;
-    (void)F;
-    (void)B;
-    (void)seeds;
-    (void)ancestors;
-    (void)stream;
-    return PF_ERR_INVALID;
+    if (!logw || !offsets || !seeds || !ancestors || F < 1 || F > (1 << 24)) return PF_ERR_INVALID;
+    if (kind < PF_MULTINOMIAL || kind > PF_METROPOLIS || (kind == PF_METROPOLIS && B < 0)) return PF_ERR_INVALID;
+    if (((uintptr_t)logw & 3u) || ((uintptr_t)ancestors & 3u) || ((uintptr_t)offsets & 7u) ||
+        ((uintptr_t)seeds & 7u))
+        return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    const int per_sm = info->batched_per_sm[kind];
+    if (per_sm < 1) return PF_ERR_CUDA;
+    const int grid = info->num_sms * per_sm;
+    const int64_t per_cta = kind == PF_MULTINOMIAL ? (int64_t)batched_scratch_floats_per_cta() : 0;
+    Workspace* w;
+    st = workspace(s, (size_t)grid * per_cta * sizeof(float), w);
+    if (st) return st;
+    BatchParams bp;
+    bp.lw = logw;
+    bp.offsets = offsets;
+    bp.F = F;
+    bp.B = B;
+    bp.seeds = seeds;
+    bp.anc = ancestors;
+    bp.ctl = w->ctl;
+    bp.scratch = (float*)w->scratch;
+    bp.scratch_per_cta = per_cta;
+    if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
+    return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
 }
 
 pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) {

@@ -1,0 +1,241 @@
+// Assignment of offsets to a tile's elements, shared by the single-launch and
+// the batched kernels (Section 2: systematic and stratified resampling give
+// offspring counts; multinomial resampling a binary search per draw).
+#pragma once
+
+#include "pf_fixed.cuh"
+#include "pf_tile.cuh"
+
+namespace pf {
+
+enum { KIND_MULTI = 0, KIND_STRAT = 1, KIND_SYS = 2 };
+constexpr int kIoCap = 8192;  // staging entries of the run-length decode
+
+struct TableEntry {  // multinomial: one tile's lower boundary and scale
+    float bhi, blo;  // B_t as a float pair (units of 2^K)
+    float sc;        // 2^(K - k_t): global units -> tile-local units
+    int il;          // last positive element of the tile, -1 if none
+};
+
+// Shared-memory fields of one filter's assignment.
+struct AssignShared {
+    i128 Wt;       // total mass W (fixed point, units of 2^K)
+    int K;         // largest tile exponent
+    int noff;      // offsets of the tile being assigned
+    long long jlo; // first offset of that tile
+    float tau0, inv_rho, W_hi, W_lo;
+    int red_n[kWarps];
+};
+
+// ---------------------------------------------------------------------------
+// Offspring-count assignment (systematic, stratified).
+// ---------------------------------------------------------------------------
+// Per-tile scalars (thread 0), in float pairs: the tile's offset range and the
+// map from tile-local cumulative weight v to the offset coordinate
+// y = v * inv_rho + x0 (offsets counted from jlo).  P <= 2^25 on this path.
+template <int KIND>
+__device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i, i128 Bh_i, int k_tile) {
+    const fpair W = {sm.W_hi, sm.W_lo};
+    const fpair Bl = fixed_to_pair(Bl_i), Bh = fixed_to_pair(Bh_i);
+    const fpair Pp = fast_two_sum((float)p.P, (float)(p.P - (int64_t)(float)p.P));  // P exactly
+    const fpair PW = pair_div(Pp, W);
+    const fpair yl = pair_mul(Bl, PW), yh = pair_mul(Bh, PW);  // B P / W
+    const bool last = Bh_i >= sm.Wt;
+    long long jl, jh;
+    float x0;
+    if (KIND == KIND_SYS) {
+        const u32x4 r = philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1);
+        const float u = u23f(r.x);
+        const fpair dl = pair_sub_f(yl, u), dh = pair_sub_f(yh, u);
+        jl = (Bl_i > 0) ? max(0LL, min((long long)p.P, pair_ceil(dl))) : 0;
+        jh = last ? p.P : max(0LL, min((long long)p.P, pair_ceil(dh)));
+        x0 = __fadd_rn(__fsub_rn(dl.hi, (float)jl), dl.lo);  // N(v) = ceil(v * inv_rho + x0)
+    } else {
+        jl = 0;
+        if (Bl_i > 0) {
+            const long long f = pair_floor(yl);
+            if (f >= p.P) {
+                jl = p.P;
+            } else {
+                const float frac = __fadd_rn(__fsub_rn(yl.hi, (float)f), yl.lo);
+                const u32x4 r = philox((uint32_t)(f >> 2), 0u, p.filter, TAG_STRAT, p.key0, p.key1);
+                jl = f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0);
+            }
+        }
+        jh = p.P;
+        if (!last) {
+            const long long f = pair_floor(yh);
+            if (f < p.P) {
+                const float frac = __fadd_rn(__fsub_rn(yh.hi, (float)f), yh.lo);
+                const u32x4 r = philox((uint32_t)(f >> 2), 0u, p.filter, TAG_STRAT, p.key0, p.key1);
+                jh = max(0LL, f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0));
+            }
+        }
+        x0 = __fadd_rn(__fsub_rn(yl.hi, (float)jl), yl.lo);  // y(v) = v * inv_rho + x0
+    }
+    sm.jlo = jl;
+    sm.noff = (int)max(0LL, jh - jl);
+    sm.tau0 = x0;
+    sm.inv_rho = PW.hi * pow2f(k_tile - sm.K);
+}
+
+template <int KIND>
+__device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_t* out, TileThread& th,
+                                 const TileSummary& ts, int64_t index0) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int noff = sm.noff;
+    const long long jlo = sm.jlo;
+    const float x0 = sm.tau0, ir = sm.inv_rho;
+    // N_i: offsets of the tile below the element's cumulative weight (kept in v[] as int bits)
+    uint32_t cq = 0xffffffffu;
+    u32x4 cw = {0, 0, 0, 0};
+    int last_n = -1;
+#pragma unroll
+    for (int i = 0; i < kMaxPerThread; ++i) {
+        if (i < th.K && ((th.pos >> i) & 1u)) {
+            int n;
+            if (th.e0 + i == ts.i_last) {
+                n = noff;
+            } else if (KIND == KIND_SYS) {
+                const float x = __fmaf_rn(th.v[i], ir, x0);
+                n = x <= 0.f ? 0 : (x >= (float)noff ? noff : min(noff, (int)ceilf(x)));
+            } else {
+                const float y = __fmaf_rn(th.v[i], ir, x0);
+                if (y <= 0.f) {
+                    n = 0;
+                } else {
+                    const float fl = floorf(y);
+                    if (fl >= (float)noff) {
+                        n = noff;
+                    } else {
+                        const long long j = jlo + (long long)fl;
+                        const uint32_t q = (uint32_t)(j >> 2);
+                        if (q != cq) {
+                            cq = q;
+                            cw = philox(q, 0u, p.filter, TAG_STRAT, p.key0, p.key1);
+                        }
+                        n = min(noff, (int)fl + (u23f(word_of(cw, (int)(j & 3))) < y - fl ? 1 : 0));
+                    }
+                }
+            }
+            th.v[i] = __int_as_float(n);
+            last_n = n;
+        }
+    }
+    // exclusive running maximum of the threads' last counts: where this thread's first run starts
+    int m = last_n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int h = __shfl_up_sync(0xffffffffu, m, o);
+        if (lane >= o) m = max(m, h);
+    }
+    int prev = __shfl_up_sync(0xffffffffu, m, 1);
+    if (lane == 0) prev = -1;
+    if (lane == 31) sm.red_n[warp] = m;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) prev = max(prev, sm.red_n[w]);
+    const int start0 = max(prev, 0);
+    const int32_t base = (int32_t)(index0 + th.e0);  // particle index of this thread's first element
+
+    // Run-length decode, one staging chunk at a time: each positive element
+    // marks the first slot of its run [N_{i-1}, N_i) with its index (runs of
+    // later elements start later, so indices increase along the chunk), the
+    // element whose run covers the chunk's first slot marks that slot, and an
+    // inclusive max-scan over the chunk fills every run.  Chunk slot s sits at
+    // out[s + shift] so that out[x] maps to the 16-byte aligned global position
+    // gb + x; each thread scans and stores 16 consecutive entries.
+    constexpr int kSlots = kIoCap / kThreads;  // entries per thread in the scan
+    constexpr int kChunk = kIoCap - 4;         // offsets per chunk (room for the shift)
+    for (int c0 = 0; c0 < noff; c0 += kChunk) {
+        const int c1 = min(noff, c0 + kChunk);
+        const int shift = (int)(((uintptr_t)(p.anc + jlo + c0) >> 2) & 3u);  // to a 16-byte boundary
+#pragma unroll
+        for (int q = 0; q < kSlots / 4; ++q)
+            *reinterpret_cast<int4*>(&out[tid * kSlots + 4 * q]) = make_int4(-1, -1, -1, -1);
+        __syncthreads();
+        int a = start0;
+#pragma unroll
+        for (int i = 0; i < kMaxPerThread; ++i) {
+            if (i < th.K && ((th.pos >> i) & 1u)) {
+                const int b = __float_as_int(th.v[i]);
+                if (b > a) {
+                    if (a >= c0 && a < c1) out[a - c0 + shift] = base + i;
+                    else if (a < c0 && b > c0) out[shift] = base + i;
+                }
+                a = b;
+            }
+        }
+        __syncthreads();
+        int4 r[kSlots / 4];
+        int run = -1;
+#pragma unroll
+        for (int q = 0; q < kSlots / 4; ++q) {
+            r[q] = *reinterpret_cast<const int4*>(&out[tid * kSlots + 4 * q]);
+            r[q].x = run = max(run, r[q].x);
+            r[q].y = run = max(run, r[q].y);
+            r[q].z = run = max(run, r[q].z);
+            r[q].w = run = max(run, r[q].w);
+        }
+        int mm = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int h = __shfl_up_sync(0xffffffffu, mm, o);
+            if (lane >= o) mm = max(mm, h);
+        }
+        int carry = __shfl_up_sync(0xffffffffu, mm, 1);
+        if (lane == 0) carry = -1;
+        if (lane == 31) sm.red_n[warp] = mm;
+        __syncthreads();
+        for (int w = 0; w < warp; ++w) carry = max(carry, sm.red_n[w]);
+        // entries x in [tid*kSlots, +kSlots) hold chunk slots x - shift
+        const int x0i = tid * kSlots;
+        const int lo = max(x0i, shift), hi = min(x0i + kSlots, shift + (c1 - c0));
+        if (hi > lo) {
+            int32_t* g = p.anc + (jlo + c0 - shift) + x0i;  // 16-byte aligned
+            int vals[kSlots];
+#pragma unroll
+            for (int q = 0; q < kSlots / 4; ++q) {
+                vals[4 * q + 0] = max(carry, r[q].x);
+                vals[4 * q + 1] = max(carry, r[q].y);
+                vals[4 * q + 2] = max(carry, r[q].z);
+                vals[4 * q + 3] = max(carry, r[q].w);
+            }
+            if (lo == x0i && hi == x0i + kSlots) {
+#pragma unroll
+                for (int q = 0; q < kSlots / 4; ++q)
+                    *reinterpret_cast<int4*>(g + 4 * q) =
+                        make_int4(vals[4 * q], vals[4 * q + 1], vals[4 * q + 2], vals[4 * q + 3]);
+            } else {
+#pragma unroll
+                for (int z = 0; z < kSlots; ++z)
+                    if (x0i + z >= lo && x0i + z < hi) g[z] = vals[z];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The tile's cumulative weights to global memory (sign bit: zero weight), for the searches.
+__device__ __forceinline__ void write_tile_v(const SortedParams& p, const TileThread& th, int64_t t0, int n) {
+    float* vg = p.v_out + t0 + th.e0;
+#pragma unroll
+    for (int q = 0; q < kMaxPerThread / 4; ++q) {
+        if (4 * q < th.K) {
+            float o[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = 4 * q + r;
+                o[r] = ((th.pos >> i) & 1u) ? th.v[i] : -th.v[i];
+            }
+            if (th.e0 + 4 * q + 3 < n) {
+                *reinterpret_cast<float4*>(vg + 4 * q) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (th.e0 + 4 * q + r < n) vg[4 * q + r] = o[r];
+            }
+        }
+    }
+}
+
+}  // namespace pf

@@ -47,8 +47,8 @@ struct TileRecord {
 };
 
 struct SortedParams {
-    const float* lw;
-    int32_t* anc;
+    const float* lw;   // 16-byte aligned base; element 0 of the filter is lw[lead]
+    int32_t* anc;      // ancestors (4-byte aligned)
     int64_t P;
     double Pd;     // P as a double
     int tile;      // elements per tile (multiple of 4, <= kTileMax)
@@ -59,11 +59,30 @@ struct SortedParams {
     uint64_t* slots;  // one 16-byte record per tile
     uint64_t wait_ns;
     int skip_tile;
-    float* v_out;     // multinomial: tile-local cumulative weights (P floats), else null
+    float* v_out;     // multinomial: tile-local cumulative weights (P + lead floats), else null
+    int lead;         // elements of the aligned window before element 0 (0..3)
+};
+
+// Batched call: F filters, filter f owns lw[offsets[f] .. offsets[f+1]).
+struct BatchParams {
+    const float* lw;
+    const int64_t* offsets;
+    int F;
+    int B;  // Metropolis steps
+    const uint64_t* seeds;
+    int32_t* anc;
+    uint32_t* ctl;
+    float* scratch;           // multinomial: per-CTA cumulative weights of multi-tile filters
+    int64_t scratch_per_cta;  // floats per CTA
 };
 
 // Kernel launchers (defined in the .cu files; return the launch error).
 cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s);
 int persistent_blocks_per_sm(int kind);
+cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s);
+int batched_blocks_per_sm(int kind);
+size_t batched_scratch_floats_per_cta();
+cudaError_t launch_batched_metropolis(const BatchParams& bp, int grid, cudaStream_t s);
+int batched_metropolis_blocks_per_sm();
 
 }  // namespace pf

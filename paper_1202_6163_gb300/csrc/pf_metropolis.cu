@@ -93,4 +93,89 @@ cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t*
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Batched: each CTA takes whole filters from a ticket counter, copies the
+// filter's log-weights to shared memory when they fit, and runs its chains
+// (filter-local indices, Philox filter id f, key seeds[f]).
+// ---------------------------------------------------------------------------
+constexpr int kMetroBThreads = 512;
+constexpr int kMetroBStage = 24 * 1024;  // floats staged per CTA (96 KiB)
+
+__global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchParams bp) {
+    extern __shared__ float wsm[];
+    __shared__ int f_sm;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) f_sm = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
+        __syncthreads();
+        const int f = f_sm;
+        __syncthreads();
+        if (f >= bp.F) break;
+        const int64_t off0 = bp.offsets[f], off1 = bp.offsets[f + 1];
+        const int64_t Pf = off1 - off0;
+        if (Pf <= 0 || Pf > 0x7fffffffLL) {
+            if (Pf != 0 && tid == 0) set_status(bp.ctl + CTL_STATUS, ST_INVALID);
+            continue;
+        }
+        const float* lw = bp.lw + off0;
+        const bool staged = Pf <= kMetroBStage;
+        if (staged) {
+            for (int64_t i = tid; i < Pf; i += kMetroBThreads) wsm[i] = __ldg(lw + i);
+            __syncthreads();
+        }
+        const uint64_t seed = bp.seeds[f];
+        const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
+        const uint32_t Pu = (uint32_t)Pf;
+        for (int64_t i = tid; i < Pf; i += kMetroBThreads) {
+            float lk = staged ? wsm[i] : __ldg(lw + i);
+            if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
+            uint32_t k = (uint32_t)i;
+            for (int b = 0; b < bp.B; b += 2) {
+                const u32x4 r = philox((uint32_t)i, (uint32_t)(b >> 1), (uint32_t)f, TAG_METRO, key0, key1);
+                {
+                    const uint32_t j = draw_index(r.x, Pu);
+                    const float lj = staged ? wsm[j] : __ldg(lw + j);
+                    if (metropolis_accept(lj, lk, u23f(r.y))) {
+                        k = j;
+                        lk = lj;
+                    }
+                }
+                if (b + 1 < bp.B) {
+                    const uint32_t j = draw_index(r.z, Pu);
+                    const float lj = staged ? wsm[j] : __ldg(lw + j);
+                    if (metropolis_accept(lj, lk, u23f(r.w))) {
+                        k = j;
+                        lk = lj;
+                    }
+                }
+            }
+            bp.anc[off0 + i] = (int32_t)k;
+        }
+        __syncthreads();  // the staging buffer is reused by the next filter
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(bp.ctl + CTL_QUEUE_DONE, 1u) == gridDim.x - 1) {
+            atomicExch(bp.ctl + CTL_QUEUE, 0u);
+            atomicExch(bp.ctl + CTL_QUEUE_DONE, 0u);
+        }
+    }
+}
+
+int batched_metropolis_blocks_per_sm() {
+    const size_t smem = kMetroBStage * sizeof(float);
+    if (cudaFuncSetAttribute(k_batched_metropolis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched_metropolis, kMetroBThreads, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_batched_metropolis(const BatchParams& bp, int grid, cudaStream_t s) {
+    k_batched_metropolis<<<grid, kMetroBThreads, kMetroBStage * sizeof(float), s>>>(bp);
+    return cudaGetLastError();
+}
+
 }  // namespace pf

@@ -50,14 +50,14 @@ __device__ __forceinline__ int per_thread_count(int n) {
 
 __device__ __forceinline__ bool zero_flag(float v) { return __float_as_uint(v) >> 31; }
 
-// Loads this thread's K elements (tile-local e0 .. e0+K) of base[0..n); base is
-// 16-byte aligned.  Out-of-range slots read as -inf.
-__device__ __forceinline__ void tile_load(const float* __restrict__ base, int n, int e0, int K,
+// Loads this thread's K elements (tile-local e0 .. e0+K) of base[lo..n); base is
+// 16-byte aligned.  Slots outside [lo, n) read as -inf (zero weight).
+__device__ __forceinline__ void tile_load(const float* __restrict__ base, int lo, int n, int e0, int K,
                                           float (&x)[kMaxPerThread]) {
 #pragma unroll
     for (int q = 0; q < kMaxPerThread / 4; ++q) {
         const int idx = e0 + 4 * q;
-        if (4 * q < K && idx + 3 < n) {
+        if (4 * q < K && idx >= lo && idx + 3 < n) {
             const float4 v = __ldg(reinterpret_cast<const float4*>(base + idx));
             x[4 * q + 0] = v.x;
             x[4 * q + 1] = v.y;
@@ -66,14 +66,15 @@ __device__ __forceinline__ void tile_load(const float* __restrict__ base, int n,
         } else {
 #pragma unroll
             for (int r = 0; r < 4; ++r)
-                x[4 * q + r] = (4 * q < K && idx + r < n) ? __ldg(base + idx + r) : -INFINITY;
+                x[4 * q + r] = (4 * q < K && idx + r >= lo && idx + r < n) ? __ldg(base + idx + r) : -INFINITY;
         }
     }
 }
 
-// Block-wide; every thread of the CTA must call it.  Fills th (this thread's
-// elements) and returns the tile summary (identical in every thread).
-__device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base, int n, TileShared& sm,
+// Block-wide; every thread of the CTA must call it.  Scans base[0..n) with the
+// first `lo` slots taken as zero weights; fills th (this thread's elements) and
+// returns the tile summary (identical in every thread).
+__device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base, int lo, int n, TileShared& sm,
                                                  TileThread& th) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = per_thread_count(n);
@@ -84,7 +85,7 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
     if (tid == 0) sm.i_last = -1;
 
     float* x = th.v;
-    tile_load(base, n, e0, K, th.v);
+    tile_load(base, lo, n, e0, K, th.v);
 
     // 1. tile maximum and domain check
     float m = -INFINITY;

@@ -1,0 +1,108 @@
+"""GPU parity of the batched call (many independent filters in one launch)
+against the oracle run filter by filter (filter f: key seeds[f], filter id f)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1202_6163_gb300 import pf, workloads
+from parity import check_cumulative, check_metropolis
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+KINDS = {"multinomial": (pf.PF_MULTINOMIAL, oracle.multinomial),
+         "stratified": (pf.PF_STRATIFIED, oracle.stratified),
+         "systematic": (pf.PF_SYSTEMATIC, oracle.systematic)}
+
+
+def run_batched(kind, lw, off, seeds, B=0):
+    d_lw = torch.from_numpy(lw).cuda()
+    d_off = torch.from_numpy(off.astype(np.int64)).cuda()
+    d_seeds = torch.from_numpy(seeds.astype(np.uint64).view(np.int64)).cuda()
+    anc = torch.full((lw.size,), -9, dtype=torch.int32, device="cuda")
+    pf.pf_resample_batched(kind, d_lw, d_off, off.size - 1, B, d_seeds, anc)
+    return anc.cpu().numpy(), pf.pf_get_device_status()
+
+
+def ragged_layout(seed=0):
+    off, sf = workloads.batched_layout(F=40, seed=seed)
+    sizes = list(np.diff(off)) + [0, 1, 2, 3, 5, 4096, 8189, 8190, 8192, 8193, 16384 + 7, 131069 - 8]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    sf = np.concatenate([sf, np.full(len(sizes) - sf.size, 1.3)])
+    return off, sf
+
+
+@pytest.mark.parametrize("name", list(KINDS))
+def test_batched_ragged_filters(name):
+    kind, orc = KINDS[name]
+    off, sf = ragged_layout(1)
+    lw = workloads.batched_logw(off, sf, seed=2)
+    seeds = workloads.batched_seeds(off.size - 1, base=1000)
+    a, st = run_batched(kind, lw, off, seeds)
+    assert st == pf.PF_OK, pf.pf_status_string(st)
+    for f in range(off.size - 1):
+        lo, hi = off[f], off[f + 1]
+        if hi == lo:
+            continue
+        l = lw[lo:hi]
+        rep = check_cumulative(name, l, a[lo:hi], orc(l, int(seeds[f]), f), int(seeds[f]), filter_id=f)
+        assert rep.ok, (f, hi - lo, rep.summary(), rep.failures[:3])
+
+
+def test_batched_metropolis_ragged_filters():
+    off, sf = ragged_layout(3)
+    lw = workloads.batched_logw(off, sf, seed=4)
+    seeds = workloads.batched_seeds(off.size - 1, base=77)
+    B = 12
+    a, st = run_batched(pf.PF_METROPOLIS, lw, off, seeds, B=B)
+    assert st == pf.PF_OK
+    for f in range(off.size - 1):
+        lo, hi = off[f], off[f + 1]
+        if hi == lo:
+            continue
+        l = lw[lo:hi]
+        rep = check_metropolis(l, B, a[lo:hi], oracle.metropolis(l, B, int(seeds[f]), f), int(seeds[f]), filter_id=f)
+        assert rep.ok, (f, rep.summary())
+
+
+def test_batched_bad_filters_are_reported_and_others_resampled():
+    sizes = [1000, 2000, 150000, 500]  # the third exceeds the per-filter limit
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    lw = workloads.gaussian_logw(int(off[-1]), 1.0, seed=5)
+    lw[off[1]:off[2]] = -np.inf  # a filter with every weight zero
+    seeds = workloads.batched_seeds(4, base=3)
+    a, st = run_batched(pf.PF_SYSTEMATIC, lw, off, seeds)
+    assert st in (pf.PF_ERR_DOMAIN, pf.PF_ERR_INVALID)
+    for f in (0, 3):
+        l = lw[off[f]:off[f + 1]]
+        rep = check_cumulative("systematic", l, a[off[f]:off[f + 1]], oracle.systematic(l, int(seeds[f]), f),
+                               int(seeds[f]), filter_id=f)
+        assert rep.ok
+
+
+@pytest.mark.parametrize("name", list(KINDS))
+def test_batched_4096_filters_sampled(name):
+    # F = 4096, P_f log-uniform in [256, 65536], s_f ~ U[0.5, 3]; 64 filters checked in full
+    kind, orc = KINDS[name]
+    off, sf = workloads.batched_layout(F=4096, seed=0)
+    lw = workloads.batched_logw(off, sf, seed=0)
+    seeds = workloads.batched_seeds(4096, base=0)
+    a, st = run_batched(kind, lw, off, seeds)
+    assert st == pf.PF_OK
+    for f in np.random.default_rng(1).choice(4096, size=64, replace=False):
+        lo, hi = off[f], off[f + 1]
+        l = lw[lo:hi]
+        rep = check_cumulative(name, l, a[lo:hi], orc(l, int(seeds[f]), int(f)), int(seeds[f]), filter_id=int(f))
+        assert rep.ok, (f, rep.summary())
+    # every ancestor is filter-local and in range
+    sizes = np.repeat(np.diff(off), np.diff(off))
+    assert np.all((a >= 0) & (a < sizes))
+
+
+def test_batched_repeatable():
+    off, sf = ragged_layout(5)
+    lw = workloads.batched_logw(off, sf, seed=6)
+    seeds = workloads.batched_seeds(off.size - 1, base=9)
+    a1, _ = run_batched(pf.PF_STRATIFIED, lw, off, seeds)
+    a2, _ = run_batched(pf.PF_STRATIFIED, lw, off, seeds)
+    assert np.array_equal(a1, a2)

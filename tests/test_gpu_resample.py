@@ -211,7 +211,7 @@ def test_invalid_arguments():
             fn(t, 0, 1, 0, a)
         assert ei.value.status == pf.PF_ERR_INVALID
         with pytest.raises(pf.PFError):
-            fn(t.data_ptr() + 4, 16, 1, 0, a)  # misaligned log-weights
+            fn(t.data_ptr() + 2, 16, 1, 0, a)  # log-weights not 4-byte aligned
         with pytest.raises(pf.PFError):
             fn(0, 16, 1, 0, a)
     with pytest.raises(pf.PFError):
@@ -312,3 +312,23 @@ def test_cumulative_beyond_single_launch_capacity_is_rejected():
     with pytest.raises(pf.PFError) as ei:
         pf.pf_resample_systematic(t, P, 0, 0, a)
     assert ei.value.status == pf.PF_ERR_INVALID
+
+
+@pytest.mark.parametrize("kind", list(CUMULATIVE))
+@pytest.mark.parametrize("off", [1, 2, 3])
+def test_unaligned_inputs(kind, off):
+    # log-weights and ancestors that start 4, 8 or 12 bytes past a 16-byte boundary
+    fn, orc = CUMULATIVE[kind]
+    for P in (5, 4099, 300001):
+        lw = workloads.gaussian_logw(P, 1.0, seed=P + off)
+        buf = torch.zeros(P + 8, device="cuda")
+        buf[off:off + P] = torch.from_numpy(lw).cuda()
+        abuf = torch.full((P + 8,), -5, dtype=torch.int32, device="cuda")
+        fn(buf.data_ptr() + 4 * off, P, 0, 3, abuf.data_ptr() + 4 * ((off + 1) % 4))
+        assert pf.pf_get_device_status() == pf.PF_OK
+        out = abuf.cpu().numpy()
+        o = (off + 1) % 4
+        a = out[o:o + P]
+        assert np.all(out[:o] == -5) and np.all(out[o + P:] == -5)
+        rep = check_cumulative(kind, lw, a, orc(lw, 3), 3)
+        assert rep.ok, rep.summary()
