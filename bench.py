@@ -269,6 +269,7 @@ def run_gpu(args):
     headline = breakdown["systematic"]
 
     e2e = run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes) if not args.no_e2e else None
+    batched = run_batched_compare(args, pf, torch, dev, stream, hbm_peak) if not args.no_batched else None
 
     launches_per_step = 6 + 0  # one kernel per entry point (the autotuned-B reduction is not used here)
     out = {
@@ -296,6 +297,7 @@ def run_gpu(args):
         "per_kernel": breakdown,
         "gpu_launches": launches_per_step * args.steps,
         "e2e": e2e,
+        "batched": batched,
         "clocks": clocks,
         "wall_s": round(wall, 3),
     }
@@ -349,6 +351,75 @@ def run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes):
     d2h = out_anc.numel() * 4 + out_st.numel() * 4 + 4
     return {"value": round(4 * P / (ms * 1e-3), 1), "unit": UNIT, "ms_per_step": round(ms, 4),
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def run_batched_compare(args, pf, torch, dev, stream, hbm_peak):
+    """Batched filters/s (one launch for F filters) against one launch per filter,
+    on F = 4096 filters with P_f log-uniform in [256, 65536] and s_f ~ U[0.5, 3]."""
+    import numpy as np
+
+    from paper_1202_6163_gb300 import workloads
+    F = 4096
+    off, sf = workloads.batched_layout(F=F, seed=0)
+    lw = torch.from_numpy(workloads.batched_logw(off, sf, seed=0)).to(dev)
+    total = int(off[-1])
+    d_off = torch.from_numpy(off).to(dev)
+    seeds = torch.from_numpy(workloads.batched_seeds(F, base=0).view(np.int64)).to(dev)
+    anc = torch.empty(total, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    kinds = {"systematic": pf.PF_SYSTEMATIC, "stratified": pf.PF_STRATIFIED, "multinomial": pf.PF_MULTINOMIAL,
+             "metropolis": pf.PF_METROPOLIS}
+    singles = {"systematic": pf.pf_resample_systematic, "stratified": pf.pf_resample_stratified,
+               "multinomial": pf.pf_resample_multinomial, "metropolis": pf.pf_resample_metropolis}
+    by_kind = {}
+    reps = 10
+    for name, kind in kinds.items():
+        B = METRO_B if kind == pf.PF_METROPOLIS else 0
+        for _ in range(2):
+            pf.pf_resample_batched(kind, lw, d_off, F, B, seeds, anc, stream)
+        torch.cuda.synchronize(dev)
+        ms = 0.0
+        for r in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pf.pf_resample_batched(kind, lw, d_off, F, B, seeds, anc, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += e0.elapsed_time(e1)
+        ms /= reps
+        # one launch per filter (each filter's slice of the same buffers; same work, F launches)
+        base_lw, base_anc = lw.data_ptr(), anc.data_ptr()
+        fn = singles[name]
+
+        def per_filter():
+            for f in range(F):
+                fn(base_lw + 4 * int(off[f]), int(off[f + 1] - off[f]), B, f, base_anc + 4 * int(off[f]), stream)
+
+        per_filter()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        per_filter()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_pf = e0.elapsed_time(e1)
+        if pf.pf_get_device_status(stream) != pf.PF_OK:
+            raise RuntimeError(f"device status not OK after batched {name}")
+        by_kind[name] = {"batched_ms": round(ms, 4), "per_filter_ms": round(ms_pf, 3),
+                         "batched_filters_per_s": round(F / (ms * 1e-3), 1),
+                         "per_filter_launch_filters_per_s": round(F / (ms_pf * 1e-3), 1),
+                         "ratio": round(ms_pf / ms, 2),
+                         "achieved_gbs": round(8 * total / (ms * 1e-3) / 1e9, 1),
+                         "hbm_frac": round(8 * total / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    head = by_kind["systematic"]
+    return {"workload": "4096 filters, P_f log-uniform in [256, 65536], log-weights N(0, s_f^2), s_f ~ U[0.5, 3]",
+            "F": F, "total_particles": total, "kind": "systematic",
+            "batched_filters_per_s": head["batched_filters_per_s"],
+            "per_filter_launch_filters_per_s": head["per_filter_launch_filters_per_s"],
+            "ratio": head["ratio"], "metropolis_B": METRO_B, "by_kind": by_kind,
+            "l2": "flushed before each timed launch (batched) / pass (per-filter)"}
 
 
 # ----------------------------------------------------------------------------- oracle arm
@@ -441,6 +512,7 @@ def main():
     ap.add_argument("--P", type=int, default=P_DEFAULT)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -213,7 +213,8 @@ pf_status pf_resample_multinomial(const float* logw, int64_t P, int B, uint64_t 
 pf_status pf_resample_metropolis(const float* logw, int64_t P, int B, uint64_t seed, int32_t* ancestors,
                                  void* stream) {
     if (!logw || !ancestors || P < 1 || P > PF_MAX_PARTICLES) return PF_ERR_INVALID;
-    if (!aligned16(logw) || !aligned16(ancestors)) return PF_ERR_INVALID;
+    if (((uintptr_t)logw & 3u) || ((uintptr_t)ancestors & 3u)) return PF_ERR_INVALID;
+    if (B < 0 && !aligned16(logw)) return PF_ERR_INVALID;  // the w_max reduction reads 16-byte vectors
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;

@@ -25,14 +25,13 @@ __device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
                                         uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t a_lo = 0xD2511F53u * c0;
-        const uint32_t a_hi = __umulhi(0xD2511F53u, c0);
-        const uint32_t b_lo = 0xCD9E8D57u * c2;
-        const uint32_t b_hi = __umulhi(0xCD9E8D57u, c2);
-        c0 = b_hi ^ c1 ^ k0;
-        c1 = b_lo;
-        c2 = a_hi ^ c3 ^ k1;
-        c3 = a_lo;
+        // one 32x32->64 product each (both halves used)
+        const uint64_t a = (uint64_t)0xD2511F53u * c0;
+        const uint64_t b = (uint64_t)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(b >> 32) ^ c1 ^ k0;
+        c1 = (uint32_t)b;
+        c2 = (uint32_t)(a >> 32) ^ c3 ^ k1;
+        c3 = (uint32_t)a;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }

@@ -24,6 +24,38 @@ __device__ __forceinline__ bool metropolis_accept(float lj, float lk, float u) {
     return u < r;
 }
 
+// B steps of chain i from state (k, lk).  The proposals do not depend on the
+// chain's state, so each group of kAhead steps draws its proposals first and
+// issues all their log-weight loads before resolving the steps in order.
+constexpr int kAhead = 8;
+
+template <bool STAGED>
+__device__ __forceinline__ void run_chain(const float* __restrict__ lw, const float* wsm, uint32_t Pu, uint32_t i,
+                                          int steps, uint32_t filter, uint32_t key0, uint32_t key1, uint32_t& k,
+                                          float& lk) {
+    for (int b0 = 0; b0 < steps; b0 += kAhead) {
+        uint32_t jj[kAhead];
+        float uu[kAhead], ll[kAhead];
+#pragma unroll
+        for (int q = 0; q < kAhead / 2; ++q) {
+            const u32x4 r = philox(i, (uint32_t)((b0 >> 1) + q), filter, TAG_METRO, key0, key1);
+            jj[2 * q] = draw_index(r.x, Pu);
+            uu[2 * q] = u23f(r.y);
+            jj[2 * q + 1] = draw_index(r.z, Pu);
+            uu[2 * q + 1] = u23f(r.w);
+        }
+#pragma unroll
+        for (int s = 0; s < kAhead; ++s) ll[s] = STAGED ? wsm[jj[s]] : __ldg(lw + jj[s]);
+#pragma unroll
+        for (int s = 0; s < kAhead; ++s) {
+            if (b0 + s < steps && metropolis_accept(ll[s], lk, uu[s])) {
+                k = jj[s];
+                lk = ll[s];
+            }
+        }
+    }
+}
+
 template <bool STAGED>
 __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __restrict__ lw, int64_t P, int B,
                                                               const uint32_t* __restrict__ B_dev, uint32_t key0,
@@ -31,11 +63,15 @@ __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __res
                                                               int32_t* __restrict__ anc, uint32_t* ctl) {
     extern __shared__ float wsm[];
     if (STAGED) {
-        // the whole log-weight vector, 16-byte copies (lw is 16-byte aligned)
-        const int n4 = (int)(P >> 2);
-        for (int q = threadIdx.x; q < n4; q += blockDim.x)
-            reinterpret_cast<float4*>(wsm)[q] = __ldg(reinterpret_cast<const float4*>(lw) + q);
-        for (int q = 4 * n4 + threadIdx.x; q < P; q += blockDim.x) wsm[q] = __ldg(lw + q);
+        // the whole log-weight vector: 16-byte copies when lw is 16-byte aligned
+        if ((((uintptr_t)lw) & 15u) == 0) {
+            const int n4 = (int)(P >> 2);
+            for (int q = threadIdx.x; q < n4; q += blockDim.x)
+                reinterpret_cast<float4*>(wsm)[q] = __ldg(reinterpret_cast<const float4*>(lw) + q);
+            for (int q = 4 * n4 + threadIdx.x; q < P; q += blockDim.x) wsm[q] = __ldg(lw + q);
+        } else {
+            for (int q = threadIdx.x; q < P; q += blockDim.x) wsm[q] = __ldg(lw + q);
+        }
         __syncthreads();
     }
     const int steps = B_dev ? (int)__ldg(B_dev) : B;
@@ -44,25 +80,7 @@ __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __res
         float lk = STAGED ? wsm[i] : __ldg(lw + i);
         if (!(lk <= 3.402823466e38f)) set_status(ctl + CTL_STATUS, ST_DOMAIN);  // NaN or +inf
         uint32_t k = (uint32_t)i;
-        for (int b = 0; b < steps; b += 2) {
-            const u32x4 r = philox((uint32_t)i, (uint32_t)(b >> 1), filter, TAG_METRO, key0, key1);
-            {
-                const uint32_t j = draw_index(r.x, Pu);
-                const float lj = STAGED ? wsm[j] : __ldg(lw + j);
-                if (metropolis_accept(lj, lk, u23f(r.y))) {
-                    k = j;
-                    lk = lj;
-                }
-            }
-            if (b + 1 < steps) {
-                const uint32_t j = draw_index(r.z, Pu);
-                const float lj = STAGED ? wsm[j] : __ldg(lw + j);
-                if (metropolis_accept(lj, lk, u23f(r.w))) {
-                    k = j;
-                    lk = lj;
-                }
-            }
-        }
+        run_chain<STAGED>(lw, wsm, Pu, (uint32_t)i, steps, filter, key0, key1, k, lk);
         anc[i] = (int32_t)k;
     }
 }
@@ -130,25 +148,8 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
             float lk = staged ? wsm[i] : __ldg(lw + i);
             if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
             uint32_t k = (uint32_t)i;
-            for (int b = 0; b < bp.B; b += 2) {
-                const u32x4 r = philox((uint32_t)i, (uint32_t)(b >> 1), (uint32_t)f, TAG_METRO, key0, key1);
-                {
-                    const uint32_t j = draw_index(r.x, Pu);
-                    const float lj = staged ? wsm[j] : __ldg(lw + j);
-                    if (metropolis_accept(lj, lk, u23f(r.y))) {
-                        k = j;
-                        lk = lj;
-                    }
-                }
-                if (b + 1 < bp.B) {
-                    const uint32_t j = draw_index(r.z, Pu);
-                    const float lj = staged ? wsm[j] : __ldg(lw + j);
-                    if (metropolis_accept(lj, lk, u23f(r.w))) {
-                        k = j;
-                        lk = lj;
-                    }
-                }
-            }
+            if (staged) run_chain<true>(lw, wsm, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k, lk);
+            else run_chain<false>(lw, wsm, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k, lk);
             bp.anc[off0 + i] = (int32_t)k;
         }
         __syncthreads();  // the staging buffer is reused by the next filter

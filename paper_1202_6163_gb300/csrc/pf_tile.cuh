@@ -7,11 +7,11 @@
 // registers, loaded with 128-bit accesses.  The tile:
 //   1. finds its largest log-weight m_t and exponent k_t ~ m_t log2 e;
 //   2. forms w_i = exp(lw_i - k_t ln 2) with an error-free subtraction;
-//   3. runs a Kahan-compensated serial scan per thread and a block scan of the
-//      per-thread totals in float pairs;
+//   3. runs a Kahan-compensated serial scan per thread and an exact block scan
+//      of the per-thread totals in 64-bit fixed point;
 //   4. leaves in registers the tile-local inclusive cumulative weights v_i
-//      (float, made monotone across threads) and a bit mask of the elements
-//      with positive weight.
+//      (float, monotone across threads) and a bit mask of the elements with
+//      positive weight.
 #pragma once
 
 #include "pf_device.cuh"
@@ -21,10 +21,8 @@ namespace pf {
 constexpr int kWarps = kThreads / 32;
 
 struct TileShared {
-    float Vb[kThreads + 1];  // per-thread bases, monotone
+    long long wtot[kWarps];  // per-warp sums of the thread totals (fixed point)
     float redf[kWarps];
-    fpair redp[kWarps];
-    fpair total;
     int i_last;
 };
 
@@ -125,43 +123,33 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
     }
     th.pos = posbits;
 
-    // block exclusive scan of the per-thread totals (float pairs)
-    const fpair tot = {s, -c};
-    const fpair inc = warp_scan_pair(tot, lane);
-    fpair ex;
-    ex.hi = __shfl_up_sync(0xffffffffu, inc.hi, 1);
-    ex.lo = __shfl_up_sync(0xffffffffu, inc.lo, 1);
-    if (lane == 0) ex = {0.f, 0.f};
-    if (lane == 31) sm.redp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const fpair wv = lane < kWarps ? sm.redp[lane] : fpair{0.f, 0.f};
-        const fpair wi = warp_scan_pair(wv, lane);
-        fpair we;
-        we.hi = __shfl_up_sync(0xffffffffu, wi.hi, 1);
-        we.lo = __shfl_up_sync(0xffffffffu, wi.lo, 1);
-        if (lane == 0) we = {0.f, 0.f};
-        if (lane < kWarps) sm.redp[lane] = we;
-        if (lane == kWarps - 1) sm.total = wi;
+    // block exclusive scan of the per-thread totals in exact 64-bit fixed point
+    // (resolution 2^-48 relative to 2^k; a tile sum is below 2^14): exact
+    // sums are monotone, and every thread knows its own next base
+    const long long tot = __float2ll_rn(s * 0x1p48f) + __float2ll_rn(-c * 0x1p48f);
+    long long inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long h = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += h;
     }
-    __syncthreads();
-    const fpair E = pair_add(sm.redp[warp], ex);
-
-    // thread bases, made monotone by a running maximum
-    float V = __fadd_rn(E.hi, E.lo);
-    V = warp_scan_max(V, lane);
-    if (lane == 31) sm.redf[warp] = V;
+    if (lane == 31) sm.wtot[warp] = inc;
     if (p >= 0) atomicMax(&sm.i_last, e0 + p);
     __syncthreads();
-    for (int w = 0; w < warp; ++w) V = fmaxf(V, sm.redf[w]);
-    sm.Vb[tid] = V;
-    const fpair S = sm.total;
-    if (tid == kThreads - 1) sm.Vb[kThreads] = fmaxf(V, __fadd_rn(S.hi, S.lo));
-    __syncthreads();
+    long long wbase = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const long long x = sm.wtot[w];
+        wbase += (w < warp) ? x : 0;
+        total += x;
+    }
+    const long long excl = wbase + inc - tot;
+    const float Vk = (float)excl * 0x1p-48f, Vn = (float)(excl + tot) * 0x1p-48f;
+    const float S_hi = (float)total;
+    const fpair S = {S_hi * 0x1p-48f, (float)(total - (long long)S_hi) * 0x1p-48f};
 
     // 4. tile-local cumulative weights; elements from the last positive one on
     // take the next base so that no gap is left between threads
-    const float Vk = sm.Vb[tid], Vn = sm.Vb[tid + 1];
 #pragma unroll
     for (int i = 0; i < kMaxPerThread; ++i) x[i] = (i >= p) ? Vn : fminf(__fadd_rn(Vk, x[i]), Vn);
 
