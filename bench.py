@@ -261,15 +261,24 @@ def run_gpu(args):
     roofline = {"kernel": dominant, "bound": "hbm", "achieved": dk["achieved_gbs"], "peak": hbm_peak,
                 "unit": "GB/s", "frac": dk["hbm_frac"], "traffic": profiled_traffic(dominant),
                 "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    # Metropolis reads one random log-weight per chain step from L2: its ceiling is
+    # the random 4-byte L2 read rate, measured live on this GPU
+    l2_rate = pf.pf_probe_l2_random_reads(lw, P, 256)
+    steps_per_s = P * METRO_B / (breakdown["metropolis"]["us"] * 1e-6)
+    breakdown["metropolis"].update({"steps_per_s": round(steps_per_s, 1),
+                                    "l2_random_reads_per_s_peak": round(l2_rate, 1),
+                                    "l2_frac": round(steps_per_s / l2_rate, 4)})
     if dominant == "metropolis":
-        steps_per_s = P * METRO_B / (dk["us"] * 1e-6)
-        roofline.update({"bound": "alu", "achieved": round(steps_per_s / 1e9, 2), "unit": "Gsteps/s",
-                         "peak": None, "frac": None,
-                         "note": "Philox-bound chain steps; peak derived in DESIGN.md"})
+        roofline.update({"bound": "l2", "achieved": round(steps_per_s * 32 / 1e9, 1), "unit": "GB/s",
+                         "peak": round(l2_rate * 32 / 1e9, 1), "frac": round(steps_per_s / l2_rate, 4),
+                         "peak_source": "measured random 4-byte L2 read rate x 32-byte sectors "
+                                        "(pf_probe_l2_random_reads, same run)",
+                         "note": "one random 4-byte log-weight read (a 32-byte L2 sector) per chain step"})
     headline = breakdown["systematic"]
 
     e2e = run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes) if not args.no_e2e else None
     batched = run_batched_compare(args, pf, torch, dev, stream, hbm_peak) if not args.no_batched else None
+    bootstrap = run_bootstrap(args, pf, torch, dev, hbm_peak) if not args.no_bootstrap else None
 
     launches_per_step = 6 + 0  # one kernel per entry point (the autotuned-B reduction is not used here)
     out = {
@@ -298,6 +307,7 @@ def run_gpu(args):
         "gpu_launches": launches_per_step * args.steps,
         "e2e": e2e,
         "batched": batched,
+        "bootstrap": bootstrap,
         "clocks": clocks,
         "wall_s": round(wall, 3),
     }
@@ -422,6 +432,97 @@ def run_batched_compare(args, pf, torch, dev, stream, hbm_peak):
             "l2": "flushed before each timed launch (batched) / pass (per-filter)"}
 
 
+def run_bootstrap(args, pf, torch, dev, hbm_peak):
+    """A whole batched bootstrap filter on the linear-Gaussian test model: 256
+    filters of P = 2^16 particles, D = 4, T = 200 steps, resampling (systematic)
+    when ESS < P/2.  Each step is two launches -- the masked batched resampler
+    and the fused propagate/weight/ESS step -- and the whole run (initial draw
+    plus T steps) is one CUDA graph, replayed."""
+    import numpy as np
+
+    from paper_1202_6163_gb300 import workloads
+    F, P, T, D = 256, 1 << 16, 200, 4
+    s = torch.cuda.Stream(dev)
+    a = torch.from_numpy(workloads.lg_params(F, seed=0)).to(dev)
+    y = torch.from_numpy(workloads.lg_observations(workloads.lg_params(F, seed=0), T=T, D=D, seed=1)).to(dev)
+    ss = torch.from_numpy(workloads.lg_step_seeds(T, F, base=1000).view(np.int64)).to(dev)
+    off = torch.arange(F + 1, dtype=torch.int64, device=dev) * P
+    x = [torch.empty((F, P, D), device=dev) for _ in range(2)]
+    lw = torch.empty((F, P), device=dev)
+    anc = torch.empty(F * P, dtype=torch.int32, device=dev)
+    ll = torch.empty(F, dtype=torch.float64, device=dev)
+    ls = torch.empty(F, dtype=torch.float64, device=dev)
+    es = torch.empty(F, device=dev)
+    rs = torch.empty(F, dtype=torch.int32, device=dev)
+    pf.pf_reserve(P, F * P, F, s)
+    stream = s.cuda_stream
+
+    def run():
+        pf.pf_lg_init(F, P, D, workloads.LG_M0, workloads.LG_P0, 0, x[0], lw, ll, ls, es, rs, stream)
+        for t in range(1, T + 1):
+            pf.pf_resample_batched_masked(pf.PF_SYSTEMATIC, lw, off, F, 0, ss[t - 1], rs, anc, stream)
+            pf.pf_lg_step(F, P, D, a, workloads.LG_Q, workloads.LG_R, 0.5, y[t - 1], t, 0, anc, x[(t - 1) % 2],
+                          x[t % 2], lw, ll, ls, es, rs, stream)
+
+    # eager pass with events around every launch: per-kernel times and the resampling rate
+    with torch.cuda.stream(s):
+        run()
+        s.synchronize()
+        evs = [None] + [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(T)]
+        flags = []
+        pf.pf_lg_init(F, P, D, workloads.LG_M0, workloads.LG_P0, 0, x[0], lw, ll, ls, es, rs, stream)
+        for t in range(1, T + 1):
+            flags.append(rs.clone())
+            evs[t][0].record(s)
+            pf.pf_resample_batched_masked(pf.PF_SYSTEMATIC, lw, off, F, 0, ss[t - 1], rs, anc, stream)
+            evs[t][1].record(s)
+            pf.pf_lg_step(F, P, D, a, workloads.LG_Q, workloads.LG_R, 0.5, y[t - 1], t, 0, anc, x[(t - 1) % 2],
+                          x[t % 2], lw, ll, ls, es, rs, stream)
+            evs[t][2].record(s)
+        s.synchronize()
+    if pf.pf_get_device_status(s) != pf.PF_OK:
+        raise RuntimeError("device status not OK after the bootstrap filter")
+    res_us = [evs[t][0].elapsed_time(evs[t][1]) * 1e3 for t in range(1, T + 1)]
+    step_us = [evs[t][1].elapsed_time(evs[t][2]) * 1e3 for t in range(1, T + 1)]
+    frac_resampled = float(torch.stack(flags).float().mean().item())
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        run()
+    reps = 5
+    with torch.cuda.stream(s):  # replay launches on the current stream
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            g.replay()
+        e1.record(s)
+    torch.cuda.synchronize(dev)
+    run_ms = e0.elapsed_time(e1) / reps
+    eager_ms = sum(evs[t][0].elapsed_time(evs[t][2]) for t in range(1, T + 1))
+    if pf.pf_get_device_status(s) != pf.PF_OK:
+        raise RuntimeError("device status not OK after the graph replays")
+    # algorithmic bytes of one step launch: read x (16 B), write x (16 B), write
+    # logw (4 B), and either read logw (no resampling) or read the ancestor (4 B)
+    step_bytes = F * P * (4 * D + 4 * D + 4 + 4)
+    st_us = statistics.median(step_us)
+    return {"workload": "256 bootstrap filters, linear-Gaussian model D=4, a_f ~ U[0.8,0.99], q=0.1, r=0.5, "
+                        "P=2^16 per filter, T=200, systematic resampling when ESS < P/2",
+            "F": F, "P": P, "T": T, "graph_nodes": 1 + 2 * T,
+            "run_ms": round(run_ms, 3), "ms_per_step": round(run_ms / T, 4),
+            "eager_steps_ms": round(eager_ms, 3),
+            "particle_steps_per_s": round(F * P * T / (run_ms * 1e-3), 1),
+            "fraction_of_filter_steps_resampled": round(frac_resampled, 4),
+            "step_kernel_us_median": round(st_us, 2),
+            "step_kernel_gbs": round(step_bytes / (st_us * 1e-6) / 1e9, 1),
+            "step_kernel_hbm_frac": round(step_bytes / (st_us * 1e-6) / 1e9 / hbm_peak, 4),
+            "step_kernel_algorithmic_bytes": step_bytes,
+            "masked_resample_us_median": round(statistics.median(res_us), 2),
+            "l2": "inputs (256 MiB of states per buffer) larger than L2"}
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_step_time(P, metro_chains, seed):
     """One step of the oracle over a bounded sample: the three cumulative resamplers, ESS
@@ -513,6 +614,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-bootstrap", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -44,10 +44,16 @@
  *    inputs and seed.
  *  - Arithmetic: FP32 log-weights and per-element work; each tile's weights
  *    are taken relative to a power of two near its maximum, so tiles combine
- *    by exact binary scaling; per-tile sums are compensated FP32 pairs and the
- *    inter-tile carries FP64.  Results agree with an FP64 evaluation of the
- *    same definitions except at decisions whose uniform lies within ~1e-6
+ *    by exact binary scaling.  Within a tile each thread keeps a compensated
+ *    FP32 running sum and the block combines the thread totals exactly in
+ *    64-bit fixed point (2^-48); the carries between tiles are exact 128-bit
+ *    fixed-point sums (2^-90), and per-tile scalars are FP32 pairs (about 48
+ *    significant bits).  Results agree with an FP64 evaluation of the same
+ *    definitions except at decisions whose uniform lies within ~1e-6
  *    (relative) of a cumulative-weight or weight-ratio threshold.
+ *  - Alignment: log-weight and ancestor arrays need 4-byte alignment (the
+ *    kernels read the 16-byte aligned window around them); pf_ess and the
+ *    autotuned Metropolis (B < 0) need 16-byte aligned log-weights.
  */
 #ifndef PF_H_
 #define PF_H_
@@ -78,18 +84,29 @@ enum {
 /* Largest P accepted by every call. */
 #define PF_MAX_PARTICLES 2147483647LL
 
+/* Largest P (plus the alignment lead of logw) of one single-filter systematic,
+ * stratified or multinomial call: 4096 tiles of 8192 log-weights. */
+#define PF_MAX_CUMULATIVE (1LL << 25)
+
+/* Largest P_f (plus the alignment lead) of one filter in a batched
+ * systematic, stratified or multinomial call: 16 tiles of 8192. */
+#define PF_MAX_BATCHED_FILTER (1LL << 17)
+
 /*
  * Systematic resampler (Figure 1c; Kitagawa 1996; Section 2).
  * One uniform u (stream tag 1, draw 0); a_j = smallest i with
  * c_i > (j + u) W / P, j = 0..P-1.  Output is non-decreasing and every
  * particle gets floor(P w_i/W) or ceil(P w_i/W) offspring.
- *   logw      [P] float, 16-byte aligned      (in)
- *   P         1 <= P <= PF_MAX_PARTICLES
+ *   logw      [P] float, 4-byte aligned       (in)
+ *   P         1 <= P and P + ((logw mod 16) / 4) <= PF_MAX_CUMULATIVE
  *   B         ignored
  *   seed      Philox key
- *   ancestors [P] int32, 16-byte aligned      (out)
- * Errors: PF_ERR_INVALID for null or misaligned pointers or P out of range;
- * device status PF_ERR_DOMAIN for NaN/+inf or all -inf log-weights.
+ *   ancestors [P] int32, 4-byte aligned       (out)
+ * One cooperative launch: every CTA scans its tiles, publishes one record per
+ * tile, waits (bounded) for all records, forms its carries and assigns its
+ * ancestors.  Errors: PF_ERR_INVALID for null or misaligned pointers or P out
+ * of range; device status PF_ERR_DOMAIN for NaN/+inf or all -inf log-weights,
+ * PF_ERR_TIMEOUT if the wait for the other CTAs' records ran out.
  */
 pf_status pf_resample_systematic(const float* logw, int64_t P, int B, uint64_t seed,
                                  int32_t* ancestors, void* stream);
@@ -163,12 +180,30 @@ pf_status pf_ess(const float* logw, int64_t P, float* ess_out, double* log_sum_o
  *   B         Metropolis steps (as pf_resample_metropolis, B >= 0 only)
  *   seeds     [F] uint64, device: filter f uses key seeds[f] and filter id f
  *   ancestors concatenated like logw; filter-local indices in [0, P_f)
- * Each filter must have P_f <= 2^31 - 1; an empty filter is skipped.
- * A filter with NaN/+inf or all -inf log-weights sets device status
+ * logw and ancestors need 4-byte alignment, offsets and seeds 8-byte.  A
+ * cumulative filter needs P_f + ((logw + offsets[f]) mod 16)/4 <=
+ * PF_MAX_BATCHED_FILTER, a Metropolis filter P_f <= 2^31 - 1; a larger one
+ * sets device status PF_ERR_INVALID and is skipped.  An empty filter is
+ * skipped.  A filter with NaN/+inf or all -inf log-weights sets device status
  * PF_ERR_DOMAIN (its ancestors are unspecified; other filters are unaffected).
  */
 pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B,
                               const uint64_t* seeds, int32_t* ancestors, void* stream);
+
+/*
+ * pf_resample_batched restricted to the filters with mask[f] != 0; the
+ * ancestors of the other filters are left untouched.  This is the
+ * resampling step of a batch of bootstrap filters that resample only when
+ * their effective sample size falls below a threshold (Section 1, steps 3-4):
+ * the mask is the per-filter decision, written on the device by the step
+ * that computed the weights, so the call can sit in a CUDA graph.
+ *   mask [F] int32, device (in)
+ * Other arguments and errors as pf_resample_batched; PF_ERR_INVALID for a
+ * NULL or misaligned mask.
+ */
+pf_status pf_resample_batched_masked(int kind, const float* logw, const int64_t* offsets, int F, int B,
+                                     const uint64_t* seeds, const int32_t* mask, int32_t* ancestors,
+                                     void* stream);
 
 /*
  * Pre-size the workspace of `stream` for single-filter calls with up to P_max
@@ -211,6 +246,16 @@ pf_status pf_set_wait_limit_ns(uint64_t ns);
  * call.  tile < 0 disarms it.
  */
 pf_status pf_debug_skip_publish(int64_t tile);
+
+/*
+ * Diagnostic (not part of the method): the rate, in reads per second, of
+ * random 4-byte reads from buf[0..n) once it is resident in L2.  This is the
+ * ceiling of the Metropolis resampler when the log-weights live in L2 (one
+ * random read per chain step).  Runs on the legacy default stream and blocks
+ * until done; buf (device, 4-byte aligned, n floats, finite values) is only
+ * read.  reads_per_thread >= 8.
+ */
+pf_status pf_probe_l2_random_reads(const float* buf, int64_t n, int reads_per_thread, double* reads_per_second);
 
 /* Largest P accepted by pf_resample_multinomial_static. */
 #define PF_STATIC_MAX_PARTICLES (1LL << 20)

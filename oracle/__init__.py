@@ -85,6 +85,14 @@ def _load():
             "orc_metropolis_matrix": (i32, [c_f, i64, c_d]),
             "orc_metropolis_B": (i64, [i64, ctypes.c_double, ctypes.c_double]),
             "orc_batched": (i32, [i32, c_f, c_i64, i32, i32, c_u64, c_i32]),
+            "orc_kalman_loglik": (ctypes.c_double, [ctypes.c_double] * 5 + [c_d, i32, i32]),
+            "orc_lg_normals": (None, [u64, u32, u32, u32, c_d]),
+            "orc_lg_init": (i32, [i32, i64, i32, ctypes.c_double, ctypes.c_double, u64, c_d, c_d, c_d, c_d, c_d,
+                                  c_i32]),
+            "orc_lg_step": (i32, [i32, i64, i32, c_f, ctypes.c_double, ctypes.c_double, ctypes.c_double, c_f, i32,
+                                  u64, c_i32, c_f, c_f, c_i32, c_d, c_d, c_d, c_d, c_d, c_d, c_d, c_i32]),
+            "orc_lg_filter": (i32, [i32, i32, i64, i32, c_f, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, c_f, i32, u64, c_u64, c_d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -287,3 +295,81 @@ def batched(kind, lw, offsets, B, seeds):
     _check(_load().orc_batched(int(kind), _p(lw, ctypes.c_float), _p(off, ctypes.c_int64), F, int(B),
                                _p(sd, ctypes.c_uint64), _p(a, ctypes.c_int32)))
     return a
+
+
+# --------------------------------------------------------------------------
+# Exact log-likelihood of the linear-Gaussian test model (Kalman filter).
+# --------------------------------------------------------------------------
+def kalman_loglik(a, q, r, y, m0=0.0, p0=1.0):
+    """log p(y_{1:T}) for D independent AR(1) dimensions; y has shape (T, D)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    T, D = y.shape
+    return float(_load().orc_kalman_loglik(float(a), float(q), float(r), float(m0), float(p0),
+                                           _p(y, ctypes.c_double), T, D))
+
+
+# --------------------------------------------------------------------------
+# Bootstrap filter on the linear-Gaussian test model (Section 1, steps 1-4):
+# x_0 ~ N(m0, p0 I), x_t = a_f x_{t-1} + N(0, q I), y_t = x_t + N(0, r I).
+# --------------------------------------------------------------------------
+TAG_PROPAGATE = 6
+
+
+def lg_normals(seed, f, j, c1):
+    """The four N(0,1) draws of Philox counter (j, c1, f, 6) (Box-Muller)."""
+    z = np.zeros(4)
+    _load().orc_lg_normals(seed, f, j, c1, _p(z, ctypes.c_double))
+    return z
+
+
+def lg_init(F, P, D, m0, p0, seed):
+    """Initial particles x [F, P, D] and filter scalars (FP64)."""
+    x = np.zeros((F, P, D))
+    lw = np.zeros((F, P))
+    ll, ls, es = np.zeros(F), np.zeros(F), np.zeros(F)
+    rs = np.zeros(F, dtype=np.int32)
+    _check(_load().orc_lg_init(F, P, D, float(m0), float(p0), seed, _p(x, ctypes.c_double),
+                               _p(lw, ctypes.c_double), _p(ll, ctypes.c_double), _p(ls, ctypes.c_double),
+                               _p(es, ctypes.c_double), _p(rs, ctypes.c_int32)))
+    return dict(x=x, logw=lw, loglik=ll, log_sum=ls, ess=es, resample=rs)
+
+
+def lg_step(a, q, r, threshold, y, t, seed, anc, x_prev, lw, resample, log_sum, loglik):
+    """One step (propagate from the ancestors where resample[f], weight,
+    log-likelihood increment, ESS and the next decision), FP64 throughout;
+    array inputs are taken as the FP32 (int32) values the caller holds."""
+    x_prev = np.ascontiguousarray(x_prev, dtype=np.float32)
+    F, P, D = x_prev.shape
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32).reshape(F, D)
+    anc = np.ascontiguousarray(anc, dtype=np.int32).reshape(F, P)
+    lw = np.ascontiguousarray(lw, dtype=np.float32).reshape(F, P)
+    resample = np.ascontiguousarray(resample, dtype=np.int32)
+    log_sum = np.ascontiguousarray(log_sum, dtype=np.float64)
+    loglik = np.ascontiguousarray(loglik, dtype=np.float64)
+    xn = np.zeros((F, P, D))
+    lo = np.zeros((F, P))
+    ll, ls, es = np.zeros(F), np.zeros(F), np.zeros(F)
+    rs = np.zeros(F, dtype=np.int32)
+    _check(_load().orc_lg_step(F, P, D, _p(a, ctypes.c_float), float(q), float(r), float(threshold),
+                               _p(y, ctypes.c_float), int(t), seed, _p(anc, ctypes.c_int32),
+                               _p(x_prev, ctypes.c_float), _p(lw, ctypes.c_float), _p(resample, ctypes.c_int32),
+                               _p(log_sum, ctypes.c_double), _p(loglik, ctypes.c_double), _p(xn, ctypes.c_double),
+                               _p(lo, ctypes.c_double), _p(ll, ctypes.c_double), _p(ls, ctypes.c_double),
+                               _p(es, ctypes.c_double), _p(rs, ctypes.c_int32)))
+    return dict(x=xn, logw=lo, loglik=ll, log_sum=ls, ess=es, resample=rs)
+
+
+def lg_filter(a, q, r, y, seed, step_seeds, P, m0=0.0, p0=1.0, threshold=0.5, kind=KIND_SYSTEMATIC):
+    """A whole bootstrap-filter run in FP64; y is [T, F, D], step_seeds [T, F].
+    Returns the log-likelihood estimates [F]."""
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    T, F, D = y.shape
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    ss = np.ascontiguousarray(step_seeds, dtype=np.uint64).reshape(-1)
+    assert ss.size >= T * F
+    ll = np.zeros(F)
+    _check(_load().orc_lg_filter(int(kind), F, P, D, _p(a, ctypes.c_float), float(q), float(r), float(m0),
+                                 float(p0), float(threshold), _p(y, ctypes.c_float), T, seed,
+                                 _p(ss, ctypes.c_uint64), _p(ll, ctypes.c_double)))
+    return ll

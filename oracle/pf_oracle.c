@@ -463,3 +463,244 @@ int orc_batched(int kind, const float* lw, const int64_t* off, int F, int B, con
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Exact log-likelihood of the linear-Gaussian test model used to check a    */
+/* whole bootstrap filter (Section 1, steps 1-4): in each of D independent   */
+/* dimensions, x_0 ~ N(m0, p0), x_t = a x_{t-1} + N(0, q), y_t = x_t +       */
+/* N(0, r).  The Kalman filter gives log p(y_{1:T}) in closed form.          */
+/* y is T x D, row-major.                                                    */
+/* ------------------------------------------------------------------------ */
+double orc_kalman_loglik(double a, double q, double r, double m0, double p0, const double* y, int T, int D)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double ll = 0.0;
+    for (int d = 0; d < D; ++d) {
+        double m = m0, p = p0;
+        for (int t = 0; t < T; ++t) {
+            /* predict */
+            double mp = a * m;
+            double pp = a * a * p + q;
+            /* observe */
+            double s = pp + r;
+            double e = y[t * D + d] - mp;
+            ll += -0.5 * (log(two_pi * s) + e * e / s);
+            /* update */
+            double k = pp / s;
+            m = mp + k * e;
+            p = (1.0 - k) * pp;
+        }
+    }
+    return ll;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bootstrap filter on the linear-Gaussian test model (Section 1, steps      */
+/* 1-4), one filter per parameter set f:                                     */
+/*   x_0 ~ N(m0, p0 I),  x_t = a_f x_{t-1} + N(0, q I),  y_t = x_t + N(0,rI) */
+/* in D dimensions (D a multiple of 4).  States are [F][P][D], log-weights   */
+/* [F][P], observations of one time [F][D].                                  */
+/*                                                                           */
+/* Noise of particle j, time t, dimension group g: Philox counter            */
+/* (j, t*(D/4) + g, f, TAG_PROPAGATE) with key = seed; its words (w0..w3)    */
+/* give four N(0,1) draws by the Box-Muller transform (Box & Muller 1958):   */
+/*   z_{4g}   = sqrt(-2 ln u(w0)) cos(2 pi u(w1)),                           */
+/*   z_{4g+1} = sqrt(-2 ln u(w0)) sin(2 pi u(w1)),  likewise (w2, w3).       */
+/* ------------------------------------------------------------------------ */
+#define TAG_PROPAGATE 6u
+
+void orc_lg_normals(uint64_t seed, uint32_t f, uint32_t j, uint32_t c1, double z[4])
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    uint32_t key[2], ctr[4], w[4];
+    seed_key(seed, key);
+    ctr[0] = j; ctr[1] = c1; ctr[2] = f; ctr[3] = TAG_PROPAGATE;
+    orc_philox4x32_10(ctr, key, w);
+    for (int h = 0; h < 2; ++h) {
+        double rad = sqrt(-2.0 * log(orc_u23(w[2 * h])));
+        double ang = two_pi * orc_u23(w[2 * h + 1]);
+        z[2 * h] = rad * cos(ang);
+        z[2 * h + 1] = rad * sin(ang);
+    }
+}
+
+/* Step 1: initial particles and filter scalars. */
+int orc_lg_init(int F, int64_t P, int D, double m0, double p0, uint64_t seed, double* x, double* lw,
+                double* loglik, double* log_sum, double* ess, int32_t* resample)
+{
+    if (F < 1 || P < 1 || D < 4 || D % 4 || p0 < 0) return ORC_ERR_INVALID;
+    double z[4];
+    for (int f = 0; f < F; ++f) {
+        for (int64_t j = 0; j < P; ++j) {
+            for (int g = 0; g < D / 4; ++g) {
+                orc_lg_normals(seed, (uint32_t)f, (uint32_t)j, (uint32_t)g, z);
+                for (int c = 0; c < 4; ++c)
+                    x[((size_t)f * P + j) * D + 4 * g + c] = m0 + sqrt(p0) * z[c];
+            }
+            lw[(size_t)f * P + j] = 0.0;
+        }
+        loglik[f] = 0.0;
+        log_sum[f] = log((double)P);
+        ess[f] = (double)P;
+        resample[f] = 0;
+    }
+    return ORC_OK;
+}
+
+/* log sum_j exp(v_j) and (sum w)^2 / sum w^2 of one filter's log-weights. */
+static int lse_ess_d(const double* v, int64_t P, double* lse, double* ess)
+{
+    double m = -INFINITY;
+    for (int64_t j = 0; j < P; ++j) {
+        if (v[j] != v[j] || v[j] == INFINITY) return ORC_ERR_DOMAIN;
+        if (v[j] > m) m = v[j];
+    }
+    if (m == -INFINITY) return ORC_ERR_DOMAIN;
+    double s = 0.0, s2 = 0.0;
+    for (int64_t j = 0; j < P; ++j) {
+        double w = exp(v[j] - m);
+        s += w;
+        s2 += w * w;
+    }
+    *lse = m + log(s);
+    *ess = s * s / s2;
+    return ORC_OK;
+}
+
+/* Steps 2-3 at time t and the resampling decision, for every filter f, with
+ * R = resample_in[f]: particle j continues from src_j = R ? anc[f*P+j] : j,
+ *   x_next = a_f x_prev[src_j] + sqrt(q) z,
+ *   lw_out = (R ? 0 : lw_in) + sum_d log N(y_d; x_next_d, r),
+ * then L = log sum exp(lw_out), loglik += L - (R ? log P : log_sum_in),
+ * ess = (sum w)^2 / sum w^2 and resample_out = (ess < threshold P).
+ * Inputs are the FP32 values a caller holds; everything else is FP64. */
+int orc_lg_step(int F, int64_t P, int D, const float* a, double q, double r, double threshold,
+                const float* y, int t, uint64_t seed, const int32_t* anc, const float* x_prev,
+                const float* lw_in, const int32_t* resample_in, const double* log_sum_in,
+                const double* loglik_in, double* x_next, double* lw_out, double* loglik_out,
+                double* log_sum_out, double* ess_out, int32_t* resample_out)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    if (F < 1 || P < 1 || D < 4 || D % 4 || q < 0 || r <= 0 || t < 1) return ORC_ERR_INVALID;
+    const int G = D / 4;
+    double z[4];
+    for (int f = 0; f < F; ++f) {
+        const int R = resample_in[f];
+        for (int64_t j = 0; j < P; ++j) {
+            int64_t src = j;
+            if (R) {
+                src = anc[(size_t)f * P + j];
+                if (src < 0 || src >= P) return ORC_ERR_INVALID;
+            }
+            double logg = 0.0;
+            for (int g = 0; g < G; ++g) {
+                orc_lg_normals(seed, (uint32_t)f, (uint32_t)j, (uint32_t)(t * G + g), z);
+                for (int c = 0; c < 4; ++c) {
+                    const int d = 4 * g + c;
+                    double xn = (double)a[f] * (double)x_prev[((size_t)f * P + src) * D + d] + sqrt(q) * z[c];
+                    x_next[((size_t)f * P + j) * D + d] = xn;
+                    double e = (double)y[(size_t)f * D + d] - xn;
+                    logg += -0.5 * log(two_pi * r) - e * e / (2.0 * r);
+                }
+            }
+            double prev = R ? 0.0 : (double)lw_in[(size_t)f * P + j];
+            lw_out[(size_t)f * P + j] = prev + logg;
+        }
+        double L, e;
+        int st = lse_ess_d(lw_out + (size_t)f * P, P, &L, &e);
+        if (st) return st;
+        double L_prev = R ? log((double)P) : log_sum_in[f];
+        loglik_out[f] = loglik_in[f] + (L - L_prev);
+        log_sum_out[f] = L;
+        ess_out[f] = e;
+        resample_out[f] = e < threshold * (double)P;
+    }
+    return ORC_OK;
+}
+
+/* Resampling of one filter with FP64 log-weights: kind 2 systematic,
+ * 1 stratified, 0 multinomial, same streams and searches as the FP32-input
+ * resamplers above. */
+static int resample_d(int kind, const double* v, int64_t P, uint64_t seed, uint32_t f, int32_t* anc, double* c,
+                      double* u)
+{
+    double m = -INFINITY;
+    for (int64_t i = 0; i < P; ++i) if (v[i] > m) m = v[i];
+    if (m == -INFINITY) return ORC_ERR_DOMAIN;
+    double run = 0.0;
+    for (int64_t i = 0; i < P; ++i) { run += exp(v[i] - m); c[i] = run; }
+    const double W = c[P - 1];
+    if (kind == 2) {
+        orc_stream_uniforms(seed, f, TAG_SYS, 1, 0, u);
+        int64_t i = 0;
+        for (int64_t j = 0; j < P; ++j) { i = walk_to(c, P, i, ((double)j + u[0]) * W / (double)P); anc[j] = (int32_t)i; }
+    } else if (kind == 1) {
+        orc_stream_uniforms(seed, f, TAG_STRAT, P, 0, u);
+        int64_t i = 0;
+        for (int64_t j = 0; j < P; ++j) { i = walk_to(c, P, i, ((double)j + u[j]) * W / (double)P); anc[j] = (int32_t)i; }
+    } else if (kind == 0) {
+        orc_stream_uniforms(seed, f, TAG_MULTI, P, 1, u);
+        for (int64_t j = 0; j < P; ++j) anc[j] = (int32_t)search(c, P, u[j] * W);
+    } else {
+        return ORC_ERR_INVALID;
+    }
+    return ORC_OK;
+}
+
+/* A whole run: step 1, then T times (step 4 for the filters that asked for
+ * it, with key step_seeds[(t-1)*F + f] and filter id f; steps 2-3).  y is
+ * [T][F][D]; loglik[f] receives the estimate of log p(y_{1:T}). */
+int orc_lg_filter(int kind, int F, int64_t P, int D, const float* a, double q, double r, double m0, double p0,
+                  double threshold, const float* y, int T, uint64_t seed, const uint64_t* step_seeds,
+                  double* loglik)
+{
+    if (F < 1 || P < 1 || D < 4 || D % 4 || T < 0) return ORC_ERR_INVALID;
+    const size_t n = (size_t)F * P;
+    double* x = (double*)malloc(sizeof(double) * n * D);
+    double* xn = (double*)malloc(sizeof(double) * n * D);
+    double* lw = (double*)malloc(sizeof(double) * n);
+    double* c = (double*)malloc(sizeof(double) * P);
+    double* u = (double*)malloc(sizeof(double) * P);
+    int32_t* anc = (int32_t*)malloc(sizeof(int32_t) * P);
+    double* log_sum = (double*)malloc(sizeof(double) * F);
+    double* ess = (double*)malloc(sizeof(double) * F);
+    int32_t* resample = (int32_t*)malloc(sizeof(int32_t) * F);
+    int st = (x && xn && lw && c && u && anc && log_sum && ess && resample) ? ORC_OK : ORC_ERR_INVALID;
+    if (!st) st = orc_lg_init(F, P, D, m0, p0, seed, x, lw, loglik, log_sum, ess, resample);
+    const int G = D / 4;
+    const double two_pi = 6.283185307179586476925286766559;
+    double z[4];
+    for (int t = 1; t <= T && !st; ++t) {
+        for (int f = 0; f < F && !st; ++f) {
+            double* lwf = lw + (size_t)f * P;
+            const int R = resample[f];
+            if (R) st = resample_d(kind, lwf, P, step_seeds[(size_t)(t - 1) * F + f], (uint32_t)f, anc, c, u);
+            for (int64_t j = 0; j < P && !st; ++j) {
+                const int64_t src = R ? anc[j] : j;
+                double logg = 0.0;
+                for (int g = 0; g < G; ++g) {
+                    orc_lg_normals(seed, (uint32_t)f, (uint32_t)j, (uint32_t)(t * G + g), z);
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int d = 4 * g + cc;
+                        double v = (double)a[f] * x[((size_t)f * P + src) * D + d] + sqrt(q) * z[cc];
+                        xn[((size_t)f * P + j) * D + d] = v;
+                        double e = (double)y[((size_t)(t - 1) * F + f) * D + d] - v;
+                        logg += -0.5 * log(two_pi * r) - e * e / (2.0 * r);
+                    }
+                }
+                lwf[j] = (R ? 0.0 : lwf[j]) + logg;
+            }
+            if (st) break;
+            double L, e;
+            st = lse_ess_d(lwf, P, &L, &e);
+            if (st) break;
+            loglik[f] += L - (R ? log((double)P) : log_sum[f]);
+            log_sum[f] = L;
+            ess[f] = e;
+            resample[f] = e < threshold * (double)P;
+        }
+        double* tmp = x; x = xn; xn = tmp;
+    }
+    free(x); free(xn); free(lw); free(c); free(u); free(anc); free(log_sum); free(ess); free(resample);
+    return st;
+}

@@ -11,6 +11,7 @@
 
 #include "pf.h"
 #include "pf_internal.h"
+#include "pf_lg.h"
 
 namespace pf {
 cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0, uint32_t key1,
@@ -21,10 +22,13 @@ cudaError_t launch_gather(const void* src, int64_t P_src, int64_t row_bytes, con
 cudaError_t launch_reduce(const float* lw, int64_t P, void* rec, uint32_t* ctl, float* ess_out, double* log_sum_out,
                           uint32_t* B_out, double eps, uint32_t B_cap, cudaStream_t s);
 int reduce_tiles(int64_t P);
+cudaError_t probe_l2_random_reads(const float* buf, int64_t n, int reads, int num_sms, double* rate);
 size_t reduce_record_bytes();
 }  // namespace pf
 
 using namespace pf;
+
+static_assert(PF_MAX_CUMULATIVE == (long long)kMaxTilesTotal * kTileMax, "single-call tile capacity");
 
 namespace {
 
@@ -44,6 +48,8 @@ struct Workspace {
     uint64_t* slots = nullptr;   // one 16-byte record per tile of the single-launch kernels
     void* scratch = nullptr;     // per-call scratch (multinomial cumulative weights, reduction records)
     size_t scratch_bytes = 0;
+    uint32_t* counters = nullptr;  // per-filter arrival counters, zero between launches
+    size_t n_counters = 0;
 };
 
 std::mutex g_mu;
@@ -112,6 +118,27 @@ pf_status workspace(cudaStream_t s, size_t scratch, Workspace*& out) {
     }
     out = &w;
     return PF_OK;
+}
+
+// At least n zeroed per-filter counters in w (allocated and cleared on growth).
+pf_status ensure_counters(Workspace& w, size_t n, cudaStream_t s) {
+    if (n <= w.n_counters) return PF_OK;
+    if (capturing(s)) return PF_ERR_NOMEM;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (w.counters) cudaFree(w.counters);
+    w.counters = nullptr;
+    w.n_counters = 0;
+    if (cudaMalloc(&w.counters, n * sizeof(uint32_t)) != cudaSuccess) return PF_ERR_NOMEM;
+    e = cudaMemsetAsync(w.counters, 0, n * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    w.n_counters = n;
+    return PF_OK;
+}
+
+size_t lg_record_bytes(int F, int64_t P) {
+    const int64_t tiles = (P + lg_tile() - 1) / lg_tile();
+    return (size_t)F * (size_t)tiles * sizeof(float4);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -274,12 +301,13 @@ pf_status pf_ess(const float* logw, int64_t P, float* ess_out, double* log_sum_o
                      "reduce launch");
 }
 
-pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B,
-                              const uint64_t* seeds, int32_t* ancestors, void* stream) {
+namespace {
+pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B, const uint64_t* seeds,
+                           const int32_t* mask, int32_t* ancestors, void* stream) {
     if (!logw || !offsets || !seeds || !ancestors || F < 1 || F > (1 << 24)) return PF_ERR_INVALID;
     if (kind < PF_MULTINOMIAL || kind > PF_METROPOLIS || (kind == PF_METROPOLIS && B < 0)) return PF_ERR_INVALID;
     if (((uintptr_t)logw & 3u) || ((uintptr_t)ancestors & 3u) || ((uintptr_t)offsets & 7u) ||
-        ((uintptr_t)seeds & 7u))
+        ((uintptr_t)seeds & 7u) || ((uintptr_t)mask & 3u))
         return PF_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -304,8 +332,21 @@ pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offset
     bp.ctl = w->ctl;
     bp.scratch = (float*)w->scratch;
     bp.scratch_per_cta = per_cta;
+    bp.mask = mask;
     if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
     return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
+}
+}  // namespace
+
+pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B,
+                              const uint64_t* seeds, int32_t* ancestors, void* stream) {
+    return resample_batched(kind, logw, offsets, F, B, seeds, nullptr, ancestors, stream);
+}
+
+pf_status pf_resample_batched_masked(int kind, const float* logw, const int64_t* offsets, int F, int B,
+                                     const uint64_t* seeds, const int32_t* mask, int32_t* ancestors, void* stream) {
+    if (!mask) return PF_ERR_INVALID;
+    return resample_batched(kind, logw, offsets, F, B, seeds, mask, ancestors, stream);
 }
 
 pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) {
@@ -319,9 +360,21 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     size_t need = (size_t)P_max * sizeof(float);
     const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
     if (red > need) need = red;
+    if (F_max > 0) {
+        const size_t batched = (size_t)info->num_sms * info->batched_per_sm[PF_MULTINOMIAL] *
+                               batched_scratch_floats_per_cta() * sizeof(float);
+        if (batched > need) need = batched;
+        // bootstrap-filter steps: one record per tile, one counter per filter
+        const size_t lg = lg_record_bytes(F_max, (total_max + F_max - 1) / F_max) + (size_t)F_max * sizeof(float4);
+        if (lg > need) need = lg;
+    }
     Workspace* w;
     st = workspace(s, need, w);
     if (st) return st;
+    if (F_max > 0) {
+        st = ensure_counters(*w, (size_t)F_max, s);
+        if (st) return st;
+    }
     return cuda_fail(cudaStreamSynchronize(s), "cudaStreamSynchronize");
 }
 
@@ -383,6 +436,113 @@ pf_status pf_debug_skip_publish(int64_t tile) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_skip_tile = tile < 0 ? -1 : tile;
     return PF_OK;
+}
+
+pf_status pf_probe_l2_random_reads(const float* buf, int64_t n, int reads_per_thread, double* reads_per_second) {
+    if (!buf || !reads_per_second || n < 1 || reads_per_thread < 8) return PF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    return cuda_fail(probe_l2_random_reads(buf, n, reads_per_thread, info->num_sms, reads_per_second), "l2 probe");
+}
+
+namespace {
+bool lg_shape_ok(int F, int64_t P, int D) {
+    return F >= 1 && F <= (1 << 24) && P >= 1 && P <= 0x7fffffffLL && D >= 4 && D <= 64 && D % 4 == 0 &&
+           (int64_t)F * P <= ((int64_t)1 << 40) && (P + 2047) / 2048 * (int64_t)F < 0x7fffffffLL;
+}
+}  // namespace
+
+pf_status pf_lg_init(int F, int64_t P, int D, float m0, float p0, uint64_t seed, float* x, float* logw,
+                     double* loglik, double* log_sum, float* ess, int32_t* resample, void* stream) {
+    if (!lg_shape_ok(F, P, D) || !(p0 >= 0.0f) || !std::isfinite(m0) || !std::isfinite(p0)) return PF_ERR_INVALID;
+    if (!x || !logw || !loglik || !log_sum || !ess || !resample) return PF_ERR_INVALID;
+    if (!aligned16(x) || ((uintptr_t)logw & 3u) || ((uintptr_t)loglik & 7u) || ((uintptr_t)log_sum & 7u) ||
+        ((uintptr_t)ess & 3u) || ((uintptr_t)resample & 3u))
+        return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    LgParams p{};
+    p.F = F;
+    p.P = P;
+    p.D = D;
+    p.sigma = (float)std::sqrt((double)p0);
+    p.m0 = m0;
+    p.log_P = std::log((double)P);
+    p.key0 = (uint32_t)(seed & 0xffffffffu);
+    p.key1 = (uint32_t)(seed >> 32);
+    p.x_next = x;
+    p.lw = logw;
+    p.loglik = loglik;
+    p.log_sum = log_sum;
+    p.ess = ess;
+    p.resample = resample;
+    return cuda_fail(launch_lg_init(p, info->num_sms, s), "lg init launch");
+}
+
+pf_status pf_lg_step(int F, int64_t P, int D, const float* a, double q, double r, double threshold,
+                     const float* y, int t, uint64_t seed, const int32_t* ancestors, const float* x_prev,
+                     float* x_next, float* logw, double* loglik, double* log_sum, float* ess, int32_t* resample,
+                     void* stream) {
+    if (!lg_shape_ok(F, P, D) || t < 1) return PF_ERR_INVALID;
+    if (!(q >= 0.0) || !(r > 0.0) || !std::isfinite(q) || !std::isfinite(r) || !(threshold >= 0.0) ||
+        !std::isfinite(threshold))
+        return PF_ERR_INVALID;
+    if (!a || !y || !ancestors || !x_prev || !x_next || !logw || !loglik || !log_sum || !ess || !resample)
+        return PF_ERR_INVALID;
+    if (x_prev == x_next) return PF_ERR_INVALID;
+    if (!aligned16(x_prev) || !aligned16(x_next) || !aligned16(y) || ((uintptr_t)a & 3u) ||
+        ((uintptr_t)ancestors & 3u) || ((uintptr_t)logw & 3u) || ((uintptr_t)loglik & 7u) ||
+        ((uintptr_t)log_sum & 7u) || ((uintptr_t)ess & 3u) || ((uintptr_t)resample & 3u))
+        return PF_ERR_INVALID;
+    // the two state buffers must not overlap
+    const uintptr_t bytes = (uintptr_t)F * (uintptr_t)P * (uintptr_t)D * sizeof(float);
+    const uintptr_t xp = (uintptr_t)x_prev, xn = (uintptr_t)x_next;
+    if (xp < xn + bytes && xn < xp + bytes) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    Workspace* w;
+    st = workspace(s, lg_record_bytes(F, P), w);
+    if (st) return st;
+    st = ensure_counters(*w, (size_t)F, s);
+    if (st) return st;
+    LgParams p{};
+    p.F = F;
+    p.P = P;
+    p.D = D;
+    p.n_tiles = (int)((P + lg_tile() - 1) / lg_tile());
+    p.a = a;
+    p.sigma = (float)std::sqrt(q);
+    p.inv2r = (float)(0.5 / r);
+    p.c_obs = (float)(-0.5 * D * std::log(6.283185307179586477 * r));
+    p.threshold = threshold;
+    p.log_P = std::log((double)P);
+    p.y = y;
+    p.t = (uint32_t)t;
+    p.key0 = (uint32_t)(seed & 0xffffffffu);
+    p.key1 = (uint32_t)(seed >> 32);
+    p.anc = ancestors;
+    p.x_prev = x_prev;
+    p.x_next = x_next;
+    p.lw = logw;
+    p.loglik = loglik;
+    p.log_sum = log_sum;
+    p.ess = ess;
+    p.resample = resample;
+    p.records = (float4*)w->scratch;
+    p.counters = w->counters;
+    p.status = w->ctl + CTL_STATUS;
+    return cuda_fail(launch_lg_step(p, s), "lg step launch");
 }
 
 int pf_version(void) { return 100; }

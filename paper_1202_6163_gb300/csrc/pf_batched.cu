@@ -11,11 +11,14 @@
 // taken as zero weights.  The last CTA to finish resets the ticket.
 #include <climits>
 
+#include "pf.h"
+
 #include "pf_assign.cuh"
 
 namespace pf {
 
-constexpr int kMaxOwnB = 16;  // tiles per filter: P_f + 3 <= 16 * kTileMax
+constexpr int kMaxOwnB = 16;  // tiles per filter: P_f + lead <= 16 * kTileMax
+static_assert(PF_MAX_BATCHED_FILTER == (long long)kMaxOwnB * kTileMax, "batched filter capacity");
 
 struct BatchShared {
     TileShared tile;
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
         const int f = sm.f;
         __syncthreads();
         if (f >= bp.F) break;
+        if (bp.mask && bp.mask[f] == 0) continue;
         const int64_t off0 = bp.offsets[f], off1 = bp.offsets[f + 1];
         const int64_t Pf = off1 - off0;
         if (Pf <= 0) {

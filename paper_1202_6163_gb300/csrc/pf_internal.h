@@ -74,10 +74,43 @@ struct BatchParams {
     uint32_t* ctl;
     float* scratch;           // multinomial: per-CTA cumulative weights of multi-tile filters
     int64_t scratch_per_cta;  // floats per CTA
+    const int32_t* mask;      // optional: filters with mask[f] == 0 are skipped
+};
+
+// One step of F bootstrap filters on the linear-Gaussian test model.
+struct LgParams {
+    int F;
+    int64_t P;
+    int D;        // multiple of 4
+    int n_tiles;  // tiles of lg_tile() particles per filter
+    const float* a;
+    float sigma;   // sqrt(q); sqrt(p0) for the initial draw
+    float m0;      // initial mean
+    float inv2r;   // 1 / (2 r)
+    float c_obs;   // -(D/2) log(2 pi r)
+    double threshold;
+    double log_P;
+    const float* y;  // [F][D] observation of this step
+    uint32_t t;
+    uint32_t key0, key1;
+    const int32_t* anc;
+    const float* x_prev;
+    float* x_next;
+    float* lw;
+    double* loglik;
+    double* log_sum;
+    float* ess;
+    int32_t* resample;
+    float4* records;     // [F][n_tiles]
+    uint32_t* counters;  // [F], zero between launches
+    uint32_t* status;
 };
 
 // Kernel launchers (defined in the .cu files; return the launch error).
 cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s);
+int lg_tile();
+cudaError_t launch_lg_init(const LgParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_lg_step(const LgParams& p, cudaStream_t s);
 int persistent_blocks_per_sm(int kind);
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s);
 int batched_blocks_per_sm(int kind);

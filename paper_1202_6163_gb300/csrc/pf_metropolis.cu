@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
         const int f = f_sm;
         __syncthreads();
         if (f >= bp.F) break;
+        if (bp.mask && bp.mask[f] == 0) continue;
         const int64_t off0 = bp.offsets[f], off1 = bp.offsets[f + 1];
         const int64_t Pf = off1 - off0;
         if (Pf <= 0 || Pf > 0x7fffffffLL) {

@@ -277,6 +277,57 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Diagnostic: the rate of random 4-byte reads from a buffer held in L2, the
+// ceiling of the Metropolis resampler at P of a few million (its chains read
+// one random log-weight per step).  Each thread makes `reads` independent
+// reads at hashed indices, eight in flight.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t probe_hash(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void __launch_bounds__(256) k_probe_l2(const float* __restrict__ buf, uint32_t n, int reads, float* sink) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.f;
+    for (int l = 0; l < reads; l += 8) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldg(buf + __umulhi(probe_hash(t * 977u + (uint32_t)(l + q) * 131071u), n));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc += v[q];
+    }
+    if (acc == -1.2345e38f) sink[0] = acc;  // keeps the loads; never true for finite data
+}
+
+cudaError_t probe_l2_random_reads(const float* buf, int64_t n, int reads, int num_sms, double* rate) {
+    if (n < 1 || n > 0xffffffffLL || reads < 8) return cudaErrorInvalidValue;
+    const int blocks = num_sms * 16;
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    float* sink = const_cast<float*>(buf);
+    k_probe_l2<<<blocks, 256>>>(buf, (uint32_t)n, reads, sink);  // warm L2
+    cudaEventRecord(a);
+    for (int r = 0; r < 5; ++r) k_probe_l2<<<blocks, 256>>>(buf, (uint32_t)n, reads, sink);
+    cudaEventRecord(b);
+    e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return e;
+    *rate = 5.0 * blocks * 256.0 * (reads & ~7) / (ms * 1e-3);
+    return cudaGetLastError();
+}
+
 int reduce_tiles(int64_t P) { return (int)((P + kRedTile - 1) / kRedTile); }
 size_t reduce_record_bytes() { return sizeof(RedRecord); }
 

@@ -38,6 +38,12 @@ SIGNATURES = {
     "pf_debug_skip_publish": (_INT, [_I64]),
     "pf_version": (_INT, []),
     "pf_resample_multinomial_static": (_INT, [_VP, _I64, _U64, _VP, _VP, _VP]),
+    "pf_probe_l2_random_reads": (_INT, [_VP, _I64, _INT, ctypes.POINTER(ctypes.c_double)]),
+    "pf_resample_batched_masked": (_INT, [_INT, _VP, _VP, _INT, _INT, _VP, _VP, _VP, _VP]),
+    "pf_lg_init": (_INT, [_INT, _I64, _INT, ctypes.c_float, ctypes.c_float, _U64, _VP, _VP, _VP, _VP, _VP, _VP,
+                          _VP]),
+    "pf_lg_step": (_INT, [_INT, _I64, _INT, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _INT, _U64,
+                          _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
 }
 
 
@@ -121,6 +127,23 @@ def pf_resample_batched(kind, logw, offsets, F, B, seeds, ancestors, stream=None
                                       _stream(stream)), "pf_resample_batched")
 
 
+def pf_resample_batched_masked(kind, logw, offsets, F, B, seeds, mask, ancestors, stream=None):
+    _check(load().pf_resample_batched_masked(kind, _ptr(logw), _ptr(offsets), F, B, _ptr(seeds), _ptr(mask),
+                                             _ptr(ancestors), _stream(stream)), "pf_resample_batched_masked")
+
+
+def pf_lg_init(F, P, D, m0, p0, seed, x, logw, loglik, log_sum, ess, resample, stream=None):
+    _check(load().pf_lg_init(F, P, D, m0, p0, seed, _ptr(x), _ptr(logw), _ptr(loglik), _ptr(log_sum), _ptr(ess),
+                             _ptr(resample), _stream(stream)), "pf_lg_init")
+
+
+def pf_lg_step(F, P, D, a, q, r, threshold, y, t, seed, ancestors, x_prev, x_next, logw, loglik, log_sum, ess,
+               resample, stream=None):
+    _check(load().pf_lg_step(F, P, D, _ptr(a), q, r, threshold, _ptr(y), t, seed, _ptr(ancestors), _ptr(x_prev),
+                             _ptr(x_next), _ptr(logw), _ptr(loglik), _ptr(log_sum), _ptr(ess), _ptr(resample),
+                             _stream(stream)), "pf_lg_step")
+
+
 def pf_reserve(P_max, total_max=0, F_max=0, stream=None):
     _check(load().pf_reserve(P_max, total_max, F_max, _stream(stream)), "pf_reserve")
 
@@ -151,6 +174,14 @@ def pf_resample_multinomial_static(logw, P, seed, ancestors, device_status=None,
     """Multinomial resampling with the library's fixed scratch array (no allocation)."""
     _check(load().pf_resample_multinomial_static(_ptr(logw), P, seed, _ptr(ancestors), _ptr(device_status),
                                                  _stream(stream)), "pf_resample_multinomial_static")
+
+
+def pf_probe_l2_random_reads(buf, n, reads_per_thread=256) -> float:
+    """Random 4-byte L2 reads per second from the device buffer buf[0..n)."""
+    out = ctypes.c_double(0.0)
+    _check(load().pf_probe_l2_random_reads(_ptr(buf), n, reads_per_thread, ctypes.byref(out)),
+           "pf_probe_l2_random_reads")
+    return out.value
 
 
 def pf_version() -> int:

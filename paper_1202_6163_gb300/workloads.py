@@ -74,3 +74,37 @@ def batched_logw(offsets: np.ndarray, spreads: np.ndarray, seed: int = 0) -> np.
 def batched_seeds(F: int, base: int = 0) -> np.ndarray:
     """Per-filter Philox seeds base + f."""
     return (np.uint64(base) + np.arange(F, dtype=np.uint64)).astype(np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# Linear-Gaussian test model for whole bootstrap-filter runs: 256 filters (one
+# per parameter set, as in particle MCMC), x_t = a_f x_{t-1} + N(0, q I),
+# y_t = x_t + N(0, r I) in D = 4 dimensions, a_f ~ U[0.8, 0.99].
+# ---------------------------------------------------------------------------
+LG_Q, LG_R, LG_M0, LG_P0 = 0.1, 0.5, 0.0, 1.0
+
+
+def lg_params(F: int = 256, lo: float = 0.8, hi: float = 0.99, seed: int = 0) -> np.ndarray:
+    """Per-filter autoregression coefficients a_f ~ U[lo, hi], float32."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=F).astype(np.float32)
+
+
+def lg_observations(a: np.ndarray, T: int = 200, D: int = 4, q: float = LG_Q, r: float = LG_R,
+                    m0: float = LG_M0, p0: float = LG_P0, seed: int = 1) -> np.ndarray:
+    """Simulate one state path per filter from the model (float64) and return the
+    observations y[t-1, f, :] of times t = 1..T as float32 [T, F, D]."""
+    rng = np.random.default_rng(seed)
+    F = a.size
+    af = a.astype(np.float64)[:, None]
+    x = m0 + math.sqrt(p0) * rng.standard_normal((F, D))
+    y = np.empty((T, F, D))
+    for t in range(T):
+        x = af * x + math.sqrt(q) * rng.standard_normal((F, D))
+        y[t] = x + math.sqrt(r) * rng.standard_normal((F, D))
+    return y.astype(np.float32)
+
+
+def lg_step_seeds(T: int, F: int, base: int = 1000) -> np.ndarray:
+    """Resampling keys: step t (1-based) of filter f uses base + t (the filter id
+    separates the filters' streams), as a uint64 [T, F] array."""
+    return np.repeat((base + np.arange(1, T + 1, dtype=np.uint64))[:, None], F, axis=1)

@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point
-include/pf.h declares (no GPU needed; no compute calls are made here)."""
+the headers under include/ declare (no GPU needed; no compute calls are made
+here)."""
 import os
 import re
 import shutil
@@ -11,13 +12,16 @@ import pytest
 import oracle
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "pf.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 def declared_symbols():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pf_[A-Za-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(pf_[A-Za-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +37,8 @@ def test_header_declares_the_boundary():
     names = declared_symbols()
     for required in ("pf_resample_multinomial", "pf_resample_stratified", "pf_resample_systematic",
                      "pf_resample_metropolis", "pf_gather", "pf_ess", "pf_resample_batched",
-                     "pf_get_device_status", "pf_metropolis_B", "pf_status_string"):
+                     "pf_get_device_status", "pf_metropolis_B", "pf_status_string",
+                     "pf_resample_batched_masked", "pf_lg_init", "pf_lg_step"):
         assert required in names
 
 

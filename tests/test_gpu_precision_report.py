@@ -1,0 +1,114 @@
+"""Precision of the FP32 path against the FP64 oracle, per workload.
+
+For each workload and resampler: the ancestor mismatch rate (every mismatch
+must be an excused near tie) and the relative error of the normalising
+constant Z = (1/P) sum_i exp(lw_i) (from pf_ess's log-sum, against the
+oracle's).  The table is printed.  Every mismatch is an excused near tie
+(a decision whose threshold lies within 1e-6 relative of the position), so
+the mismatch count is bounded by the number of in-band decisions; with nearly
+uniform weights (s = 0.25 at P = 2^20) the threshold spacing is itself about
+1e-6 and most decisions are in band.  |log Z error| stays below 2e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1202_6163_gb300 import pf, workloads
+from parity import check_cumulative, check_metropolis
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FNS = {"systematic": (pf.pf_resample_systematic, oracle.systematic),
+       "stratified": (pf.pf_resample_stratified, oracle.stratified),
+       "multinomial": (pf.pf_resample_multinomial, oracle.multinomial)}
+
+
+def log_z_error(lw):
+    d = torch.from_numpy(lw).cuda()
+    e = torch.zeros(1, device="cuda")
+    ls = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pf.pf_ess(d, lw.size, e, ls)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    return ls.item() - oracle.ess(lw)[1]
+
+
+def single(name, lw, seed):
+    fn, orc = FNS[name]
+    d = torch.from_numpy(lw).cuda()
+    a = torch.empty(lw.size, dtype=torch.int32, device="cuda")
+    fn(d, lw.size, 0, seed, a)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    rep = check_cumulative(name, lw, a.cpu().numpy(), orc(lw, seed), seed)
+    assert rep.ok, rep.summary()
+    return rep
+
+
+WORKLOADS = [
+    ("P=1024 N(0,1)", lambda: workloads.gaussian_logw(1024, 1.0, seed=0)),
+    ("P=2^20 N(0,0.25^2)", lambda: workloads.gaussian_logw(1 << 20, 0.25, seed=25)),
+    ("P=2^20 N(0,1)", lambda: workloads.gaussian_logw(1 << 20, 1.0, seed=100)),
+    ("P=2^20 N(0,2^2)", lambda: workloads.gaussian_logw(1 << 20, 2.0, seed=200)),
+    ("P=2^20 N(0,4^2)", lambda: workloads.gaussian_logw(1 << 20, 4.0, seed=400)),
+    ("P=2^24 heavy tail", lambda: workloads.heavy_tail_logw(1 << 24, 10.0, 0.01, seed=3)),
+]
+
+
+def test_precision_report():
+    rows = []
+    for label, make in WORKLOADS:
+        lw = make()
+        dz = log_z_error(lw)
+        assert abs(dz) < 2e-6, (label, dz)
+        for name in FNS:
+            rep = single(name, lw, seed=17)
+            rate = rep.mismatches / lw.size
+            assert rep.mismatches <= rep.in_band, (label, name, rep.summary())
+            worst = max((r[5] for r in rep.excused), default=0.0)
+            rows.append((label, name, rep.mismatches, rate, worst, dz, rep.in_band / lw.size))
+        # Metropolis, B = 32, on sampled chains
+        B = 32
+        d = torch.from_numpy(lw).cuda()
+        a = torch.empty(lw.size, dtype=torch.int32, device="cuda")
+        pf.pf_resample_metropolis(d, lw.size, B, 17, a)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        idx = np.unique(np.random.default_rng(0).integers(0, lw.size, size=min(lw.size, 4000)))
+        rep = check_metropolis(lw, B, a.cpu().numpy()[idx], oracle.metropolis(lw, B, 17, chains=idx), 17, chains=idx)
+        assert rep.ok, rep.summary()
+        rows.append((label, "metropolis(B=32, sampled)", rep.mismatches, rep.mismatches / idx.size, float("nan"), dz,
+                     float("nan")))
+    print("\nworkload | resampler | mismatches | rate | worst |x-theta|/theta | log Z error | in-band fraction")
+    for r in rows:
+        print(f"{r[0]} | {r[1]} | {r[2]} | {r[3]:.2e} | {r[4]:.2e} | {r[5]:.2e} | {r[6]:.2e}")
+
+
+def test_precision_batched_4096():
+    off, sf = workloads.batched_layout(F=4096, seed=0)
+    lw = workloads.batched_logw(off, sf, seed=0)
+    seeds = workloads.batched_seeds(4096, base=0)
+    d_lw = torch.from_numpy(lw).cuda()
+    d_off = torch.from_numpy(off).cuda()
+    d_seeds = torch.from_numpy(seeds.view(np.int64)).cuda()
+    anc = torch.empty(lw.size, dtype=torch.int32, device="cuda")
+    total_mis, total_n = 0, 0
+    for name, kind in (("systematic", pf.PF_SYSTEMATIC), ("stratified", pf.PF_STRATIFIED),
+                       ("multinomial", pf.PF_MULTINOMIAL)):
+        pf.pf_resample_batched(kind, d_lw, d_off, 4096, 0, d_seeds, anc)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        a = anc.cpu().numpy()
+        mis = n = band = 0
+        for f in range(0, 4096, 16):  # every 16th filter in full
+            lo, hi = off[f], off[f + 1]
+            l = lw[lo:hi]
+            rep = check_cumulative(name, l, a[lo:hi], FNS[name][1](l, int(seeds[f]), f), int(seeds[f]), filter_id=f)
+            assert rep.ok, (f, rep.summary())
+            mis += rep.mismatches
+            band += rep.in_band
+            n += hi - lo
+        print(f"batched 4096 filters | {name} | {mis} mismatches in {n} ancestors | rate {mis / n:.2e} "
+              f"| in-band fraction {band / n:.2e}")
+        assert mis <= band
+        total_mis += mis
+        total_n += n
