@@ -150,6 +150,14 @@ def run_gpu(args):
     pf.load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.only:
+        # one secondary leg alone (used for profiling); prints that leg's JSON only
+        hbm_peak, _ = load_peaks()
+        leg = {"batched": lambda: run_batched_compare(args, pf, torch, dev, stream, hbm_peak),
+               "bootstrap": lambda: run_bootstrap(args, pf, torch, dev, hbm_peak)}[args.only]()
+        if rank == 0:
+            print(json.dumps({"leg": args.only, **leg}))
+        return
     P = args.P
     lw_h = workloads.gaussian_logw(P, SPREAD, seed=SEED + rank)
     st_h = workloads.states(P, D_STATE, seed=SEED + 1 + rank)
@@ -165,6 +173,14 @@ def run_gpu(args):
     seed_box = [SEED]
 
     kernels = ["ess", "systematic", "stratified", "multinomial", "metropolis", "gather"]
+
+    # tile sizes of the single-launch resamplers from the library's autotuner (untimed)
+    tuned = {}
+    if not args.no_autotune:
+        for name, kind in (("systematic", pf.PF_SYSTEMATIC), ("stratified", pf.PF_STRATIFIED),
+                           ("multinomial", pf.PF_MULTINOMIAL)):
+            tile, us = pf.pf_autotune(kind, lw, P, anc["sys"], 20, stream)
+            tuned[name] = {"min_tile": tile, "tuning_median_us": round(us, 2)}
 
     def step(evs=None):
         s = seed_box[0]
@@ -298,6 +314,7 @@ def run_gpu(args):
                                "ess + systematic + stratified + multinomial + metropolis(B=32) + gather",
                    "P": P, "state_dim": D_STATE, "metropolis_B": METRO_B, "spread": SPREAD,
                    "l2": "flushed between steps (256 MiB write, outside the timed interval)",
+                   "autotuned_tiles": tuned,
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "headline_systematic": {"ancestors_per_s": round(P / (headline["us"] * 1e-6), 1),
@@ -615,6 +632,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-bootstrap", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--only", choices=["batched", "bootstrap"], default=None,
+                    help="run one secondary leg alone and print its JSON (for profiling)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -213,6 +213,32 @@ pf_status pf_resample_batched_masked(int kind, const float* logw, const int64_t*
 pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream);
 
 /*
+ * Tile-size autotuner for the single-launch systematic, stratified and
+ * multinomial calls (the paper has no counterpart: its kernels were tuned by
+ * hand for one GPU).  While P fits one tile per resident CTA, a call splits
+ * the log-weights into tiles of at least `min_tile` (fewer, larger tiles mean
+ * fewer records to combine but less parallel work per element); the choice is
+ * kept per (device, kind, size class ceil(log2 P)) in this process.
+ *
+ * pf_autotune times `kind` on the caller's log-weights for each candidate
+ * min_tile in {1024, 1536, 2048, 3072, 4096, 6144, 8192} (2 warm-up calls and
+ * `reps` timed calls each, CUDA events on `stream`, median), keeps the fastest
+ * for P's size class and returns it in *min_tile_out (and its median time in
+ * microseconds in *us_out; either may be NULL).  Synchronous; overwrites
+ * `ancestors`; arguments as pf_resample_systematic, 1 <= reps <= 1000.
+ * PF_ERR_INVALID while `stream` is capturing a graph.
+ *
+ * pf_set_min_tile stores a choice (e.g. one tuned in an earlier process;
+ * 0 restores the default of 2048); pf_get_min_tile returns the value in
+ * effect (-1 for bad arguments).  The environment variable PF_MIN_TILE, when
+ * set, overrides both.
+ */
+pf_status pf_autotune(int kind, const float* logw, int64_t P, int32_t* ancestors, int reps, void* stream,
+                      int* min_tile_out, float* us_out);
+pf_status pf_set_min_tile(int kind, int64_t P, int min_tile);
+int pf_get_min_tile(int kind, int64_t P);
+
+/*
  * Synchronise `stream`, return in *out the first device-side error recorded
  * by calls on it since the last read (PF_OK if none), and clear it.
  */

@@ -8,6 +8,8 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
+#include <algorithm>
 
 #include "pf.h"
 #include "pf_internal.h"
@@ -149,12 +151,10 @@ size_t reduce_scratch(int64_t P) { return (size_t)reduce_tiles(P) * reduce_recor
 // multiple of 4, at most kTileMax), R consecutive tiles per CTA, G <= G_max
 // resident CTAs.  While P fits one tile per resident CTA, tiles hold at least
 // ~2K log-weights and R = 1; beyond that tiles are full and R grows.
-bool persistent_layout(int64_t P, int G_max, int& G, int& tile, int& T, int& R) {
+bool persistent_layout(int64_t P, int G_max, int64_t min_tile, int& G, int& tile, int& T, int& R) {
     if (G_max < 1) return false;
     if (P > (int64_t)kMaxTilesTotal * kTileMax) return false;
     if (P <= (int64_t)G_max * kTileMax) {
-        const char* env = std::getenv("PF_MIN_TILE");
-        int64_t min_tile = env ? std::atoll(env) : 2048;
         if (min_tile < 4) min_tile = 4;
         int64_t g = (P + min_tile - 1) / min_tile;
         if (g > G_max) g = G_max;
@@ -175,6 +175,24 @@ bool persistent_layout(int64_t P, int G_max, int& G, int& tile, int& T, int& R) 
     return R <= 64;
 }
 
+// Minimum tile size of the single-launch kernels per (device, kind, size
+// class ceil(log2 P)); 0 = the default.  Set by pf_autotune / pf_set_min_tile.
+constexpr int kSizeClasses = 32;
+constexpr int kDefaultMinTile = 2048;
+int g_min_tile[kMaxDevices][3][kSizeClasses] = {};
+
+int size_class(int64_t P) {
+    int c = 0;
+    while (c < kSizeClasses - 1 && ((int64_t)1 << c) < P) ++c;
+    return c;
+}
+
+int64_t min_tile_for(int dev, int kind, int64_t P) {
+    if (const char* env = std::getenv("PF_MIN_TILE")) return std::atoll(env);
+    const int t = g_min_tile[dev][kind][size_class(P)];
+    return t > 0 ? t : kDefaultMinTile;
+}
+
 pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t seed, int32_t* anc, void* stream) {
     if (!logw || !anc || P < 1 || P > PF_MAX_PARTICLES) return PF_ERR_INVALID;
     if (((uintptr_t)logw & 3u) || ((uintptr_t)anc & 3u)) return PF_ERR_INVALID;
@@ -188,7 +206,8 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     pf_status st = device_info(dev, info);
     if (st) return st;
     int G, tile, T, R;
-    if (!persistent_layout(PA, info->num_sms * info->persist_per_sm[kind], G, tile, T, R)) {
+    if (!persistent_layout(PA, info->num_sms * info->persist_per_sm[kind], min_tile_for(dev, kind, P), G, tile, T,
+                           R)) {
         return PF_ERR_INVALID;  // P beyond kMaxTilesTotal full tiles
     }
     Workspace* w;
@@ -543,6 +562,89 @@ pf_status pf_lg_step(int F, int64_t P, int D, const float* a, double q, double r
     p.counters = w->counters;
     p.status = w->ctl + CTL_STATUS;
     return cuda_fail(launch_lg_step(p, s), "lg step launch");
+}
+
+pf_status pf_set_min_tile(int kind, int64_t P, int min_tile) {
+    if (kind < PF_MULTINOMIAL || kind > PF_SYSTEMATIC || P < 1 || min_tile < 0 || min_tile > kTileMax)
+        return PF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return PF_ERR_CUDA;
+    g_min_tile[dev][kind][size_class(P)] = min_tile;
+    return PF_OK;
+}
+
+int pf_get_min_tile(int kind, int64_t P) {
+    if (kind < PF_MULTINOMIAL || kind > PF_SYSTEMATIC || P < 1) return -1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    return (int)min_tile_for(dev, kind, P);
+}
+
+pf_status pf_autotune(int kind, const float* logw, int64_t P, int32_t* ancestors, int reps, void* stream,
+                      int* min_tile_out, float* us_out) {
+    static const int kCandidates[] = {1024, 1536, 2048, 3072, 4096, 6144, 8192};
+    if (kind < PF_MULTINOMIAL || kind > PF_SYSTEMATIC || reps < 1 || reps > 1000) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return PF_ERR_INVALID;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return PF_ERR_CUDA;
+    const int cls = size_class(P);
+    int saved;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        saved = g_min_tile[dev][kind][cls];
+    }
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return PF_ERR_CUDA;
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return PF_ERR_CUDA;
+    }
+    std::vector<float> times;
+    int best = 0;
+    float best_us = 0.0f;
+    pf_status st = PF_OK;
+    for (int c : kCandidates) {
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            g_min_tile[dev][kind][cls] = c;
+        }
+        times.clear();
+        for (int r = 0; r < reps + 2 && st == PF_OK; ++r) {
+            e = cudaEventRecord(ev[0], s);
+            if (e == cudaSuccess) {
+                st = resample_cumulative(kind, logw, P, (uint64_t)r, ancestors, stream);
+                if (st) break;
+                e = cudaEventRecord(ev[1], s);
+            }
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (e != cudaSuccess) st = cuda_fail(e, "autotune timing");
+            if (r >= 2) times.push_back(ms * 1e3f);  // two warm-up calls per candidate
+        }
+        if (st) break;
+        std::sort(times.begin(), times.end());
+        const float med = times[times.size() / 2];
+        if (best == 0 || med < best_us) {
+            best = c;
+            best_us = med;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_min_tile[dev][kind][cls] = st == PF_OK ? best : saved;
+    if (st) return st;
+    if (min_tile_out) *min_tile_out = best;
+    if (us_out) *us_out = best_us;
+    return PF_OK;
 }
 
 int pf_version(void) { return 100; }

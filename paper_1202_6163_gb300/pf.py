@@ -39,6 +39,10 @@ SIGNATURES = {
     "pf_version": (_INT, []),
     "pf_resample_multinomial_static": (_INT, [_VP, _I64, _U64, _VP, _VP, _VP]),
     "pf_probe_l2_random_reads": (_INT, [_VP, _I64, _INT, ctypes.POINTER(ctypes.c_double)]),
+    "pf_autotune": (_INT, [_INT, _VP, _I64, _VP, _INT, _VP, ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_float)]),
+    "pf_set_min_tile": (_INT, [_INT, _I64, _INT]),
+    "pf_get_min_tile": (_INT, [_INT, _I64]),
     "pf_resample_batched_masked": (_INT, [_INT, _VP, _VP, _INT, _INT, _VP, _VP, _VP, _VP]),
     "pf_lg_init": (_INT, [_INT, _I64, _INT, ctypes.c_float, ctypes.c_float, _U64, _VP, _VP, _VP, _VP, _VP, _VP,
                           _VP]),
@@ -142,6 +146,23 @@ def pf_lg_step(F, P, D, a, q, r, threshold, y, t, seed, ancestors, x_prev, x_nex
     _check(load().pf_lg_step(F, P, D, _ptr(a), q, r, threshold, _ptr(y), t, seed, _ptr(ancestors), _ptr(x_prev),
                              _ptr(x_next), _ptr(logw), _ptr(loglik), _ptr(log_sum), _ptr(ess), _ptr(resample),
                              _stream(stream)), "pf_lg_step")
+
+
+def pf_autotune(kind, logw, P, ancestors, reps=20, stream=None):
+    """Returns (min_tile, median microseconds) of the fastest candidate."""
+    t = ctypes.c_int(0)
+    us = ctypes.c_float(0)
+    _check(load().pf_autotune(kind, _ptr(logw), P, _ptr(ancestors), reps, _stream(stream), ctypes.byref(t),
+                              ctypes.byref(us)), "pf_autotune")
+    return t.value, us.value
+
+
+def pf_set_min_tile(kind, P, min_tile):
+    _check(load().pf_set_min_tile(kind, P, min_tile), "pf_set_min_tile")
+
+
+def pf_get_min_tile(kind, P) -> int:
+    return load().pf_get_min_tile(kind, P)
 
 
 def pf_reserve(P_max, total_max=0, F_max=0, stream=None):
