@@ -79,6 +79,78 @@ __device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i,
     sm.inv_rho = PW.hi * pow2f(k_tile - sm.K);
 }
 
+// One chunk [c0, c1) of the tile's offsets: each positive element marks the
+// first slot of its run [N_{i-1}, N_i) with its index (runs of later elements
+// start later, so indices increase along the chunk), the element whose run
+// covers the chunk's first slot marks that slot, and an inclusive max-scan
+// over the chunk fills every run.  Chunk slot s sits at out[s + shift] so that
+// out[x] maps to the 16-byte aligned global position gb + x; each thread scans
+// and stores S consecutive entries (S * kThreads >= c1 - c0 + shift).
+template <int S>
+__device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared& sm, int32_t* out,
+                                             const TileThread& th, long long jlo, int c0, int c1, int shift,
+                                             int start0, int32_t base) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x0i = tid * S;
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) *reinterpret_cast<int4*>(&out[x0i + 4 * q]) = make_int4(-1, -1, -1, -1);
+    __syncthreads();
+    int a = start0;
+#pragma unroll
+    for (int i = 0; i < kMaxPerThread; ++i) {
+        if (i < th.K && ((th.pos >> i) & 1u)) {
+            const int b = __float_as_int(th.v[i]);
+            if (b > a) {
+                if (a >= c0 && a < c1) out[a - c0 + shift] = base + i;
+                else if (a < c0 && b > c0) out[shift] = base + i;
+            }
+            a = b;
+        }
+    }
+    __syncthreads();
+    int4 r[S / 4];
+    int run = -1;
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) {
+        r[q] = *reinterpret_cast<const int4*>(&out[x0i + 4 * q]);
+        r[q].x = run = max(run, r[q].x);
+        r[q].y = run = max(run, r[q].y);
+        r[q].z = run = max(run, r[q].z);
+        r[q].w = run = max(run, r[q].w);
+    }
+    int mm = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int h = __shfl_up_sync(0xffffffffu, mm, o);
+        if (lane >= o) mm = max(mm, h);
+    }
+    int carry = __shfl_up_sync(0xffffffffu, mm, 1);
+    if (lane == 0) carry = -1;
+    if (lane == 31) sm.red_n[warp] = mm;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) carry = max(carry, sm.red_n[w]);
+    // entries x in [x0i, x0i + S) hold chunk slots x - shift
+    const int lo = max(x0i, shift), hi = min(x0i + S, shift + (c1 - c0));
+    if (hi > lo) {
+        int32_t* g = p.anc + (jlo + c0 - shift) + x0i;  // 16-byte aligned
+        if (lo == x0i && hi == x0i + S) {
+#pragma unroll
+            for (int q = 0; q < S / 4; ++q)
+                *reinterpret_cast<int4*>(g + 4 * q) = make_int4(max(carry, r[q].x), max(carry, r[q].y),
+                                                                 max(carry, r[q].z), max(carry, r[q].w));
+        } else {
+#pragma unroll
+            for (int q = 0; q < S / 4; ++q) {
+                const int v4[4] = {max(carry, r[q].x), max(carry, r[q].y), max(carry, r[q].z), max(carry, r[q].w)};
+#pragma unroll
+                for (int z = 0; z < 4; ++z)
+                    if (x0i + 4 * q + z >= lo && x0i + 4 * q + z < hi) g[4 * q + z] = v4[z];
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <int KIND>
 __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_t* out, TileThread& th,
                                  const TileSummary& ts, int64_t index0) {
@@ -137,81 +209,19 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
     const int start0 = max(prev, 0);
     const int32_t base = (int32_t)(index0 + th.e0);  // particle index of this thread's first element
 
-    // Run-length decode, one staging chunk at a time: each positive element
-    // marks the first slot of its run [N_{i-1}, N_i) with its index (runs of
-    // later elements start later, so indices increase along the chunk), the
-    // element whose run covers the chunk's first slot marks that slot, and an
-    // inclusive max-scan over the chunk fills every run.  Chunk slot s sits at
-    // out[s + shift] so that out[x] maps to the 16-byte aligned global position
-    // gb + x; each thread scans and stores 16 consecutive entries.
-    constexpr int kSlots = kIoCap / kThreads;  // entries per thread in the scan
-    constexpr int kChunk = kIoCap - 4;         // offsets per chunk (room for the shift)
+    // Run-length decode, one staging chunk at a time (decode_chunk); chunks
+    // of at most 2044 / 4092 offsets use 4 / 8 staging entries per thread.
+    constexpr int kChunk = kIoCap - 4;  // offsets per chunk (room for the shift)
     for (int c0 = 0; c0 < noff; c0 += kChunk) {
         const int c1 = min(noff, c0 + kChunk);
         const int shift = (int)(((uintptr_t)(p.anc + jlo + c0) >> 2) & 3u);  // to a 16-byte boundary
-#pragma unroll
-        for (int q = 0; q < kSlots / 4; ++q)
-            *reinterpret_cast<int4*>(&out[tid * kSlots + 4 * q]) = make_int4(-1, -1, -1, -1);
-        __syncthreads();
-        int a = start0;
-#pragma unroll
-        for (int i = 0; i < kMaxPerThread; ++i) {
-            if (i < th.K && ((th.pos >> i) & 1u)) {
-                const int b = __float_as_int(th.v[i]);
-                if (b > a) {
-                    if (a >= c0 && a < c1) out[a - c0 + shift] = base + i;
-                    else if (a < c0 && b > c0) out[shift] = base + i;
-                }
-                a = b;
-            }
-        }
-        __syncthreads();
-        int4 r[kSlots / 4];
-        int run = -1;
-#pragma unroll
-        for (int q = 0; q < kSlots / 4; ++q) {
-            r[q] = *reinterpret_cast<const int4*>(&out[tid * kSlots + 4 * q]);
-            r[q].x = run = max(run, r[q].x);
-            r[q].y = run = max(run, r[q].y);
-            r[q].z = run = max(run, r[q].z);
-            r[q].w = run = max(run, r[q].w);
-        }
-        int mm = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int h = __shfl_up_sync(0xffffffffu, mm, o);
-            if (lane >= o) mm = max(mm, h);
-        }
-        int carry = __shfl_up_sync(0xffffffffu, mm, 1);
-        if (lane == 0) carry = -1;
-        if (lane == 31) sm.red_n[warp] = mm;
-        __syncthreads();
-        for (int w = 0; w < warp; ++w) carry = max(carry, sm.red_n[w]);
-        // entries x in [tid*kSlots, +kSlots) hold chunk slots x - shift
-        const int x0i = tid * kSlots;
-        const int lo = max(x0i, shift), hi = min(x0i + kSlots, shift + (c1 - c0));
-        if (hi > lo) {
-            int32_t* g = p.anc + (jlo + c0 - shift) + x0i;  // 16-byte aligned
-            int vals[kSlots];
-#pragma unroll
-            for (int q = 0; q < kSlots / 4; ++q) {
-                vals[4 * q + 0] = max(carry, r[q].x);
-                vals[4 * q + 1] = max(carry, r[q].y);
-                vals[4 * q + 2] = max(carry, r[q].z);
-                vals[4 * q + 3] = max(carry, r[q].w);
-            }
-            if (lo == x0i && hi == x0i + kSlots) {
-#pragma unroll
-                for (int q = 0; q < kSlots / 4; ++q)
-                    *reinterpret_cast<int4*>(g + 4 * q) =
-                        make_int4(vals[4 * q], vals[4 * q + 1], vals[4 * q + 2], vals[4 * q + 3]);
-            } else {
-#pragma unroll
-                for (int z = 0; z < kSlots; ++z)
-                    if (x0i + z >= lo && x0i + z < hi) g[z] = vals[z];
-            }
-        }
-        __syncthreads();
+        const int need = c1 - c0 + shift;
+        if (need <= 4 * kThreads)
+            decode_chunk<4>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+        else if (need <= 8 * kThreads)
+            decode_chunk<8>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+        else
+            decode_chunk<16>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
     }
 }
 

@@ -109,37 +109,52 @@ __global__ void __launch_bounds__(kLgThreads) k_lg_init(LgParams p) {
     }
 }
 
+// GS > 0: D = 4 GS known at compile time; GS = 0: D from the parameters.
+template <int GS>
 __global__ void __launch_bounds__(kLgThreads) k_lg_step(LgParams p) {
     __shared__ float ra[kLgWarps], rb[kLgWarps];
     __shared__ int last;
     const int f = (int)(blockIdx.x / (unsigned)p.n_tiles);
     const int tile = (int)(blockIdx.x - (unsigned)f * (unsigned)p.n_tiles);
     const int tid = threadIdx.x;
-    const int G = p.D >> 2;
+    const int G = GS > 0 ? GS : (p.D >> 2);
+    const int D = 4 * G;
     const int64_t base = (int64_t)f * p.P;
     const int rf = __ldcg(p.resample + f);
     const float a = __ldg(p.a + f);
-    const float* yf = p.y + (int64_t)f * p.D;
+    const float* yf = p.y + (int64_t)f * D;
     const uint32_t c1 = p.t * (uint32_t)G;
 
-    float v[kLgPerThread];
-    float m = -INFINITY;
+    // loads first (ancestors, then the rows they select, then old log-weights)
+    int64_t jj[kLgPerThread], src[kLgPerThread];
     bool bad_anc = false, bad_w = false;
 #pragma unroll
     for (int k = 0; k < kLgPerThread; ++k) {
-        const int64_t j = (int64_t)tile * (kLgThreads * kLgPerThread) + k * kLgThreads + tid;
+        jj[k] = (int64_t)tile * (kLgThreads * kLgPerThread) + k * kLgThreads + tid;
+        src[k] = jj[k];
+        if (rf && jj[k] < p.P) {
+            const int32_t q = __ldcs(p.anc + base + jj[k]);
+            if (q < 0 || q >= p.P) bad_anc = true;
+            else src[k] = q;
+        }
+    }
+    float prev[kLgPerThread];
+#pragma unroll
+    for (int k = 0; k < kLgPerThread; ++k) prev[k] = (!rf && jj[k] < p.P) ? p.lw[base + jj[k]] : 0.0f;
+
+    float v[kLgPerThread];
+    float m = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < kLgPerThread; ++k) {
+        const int64_t j = jj[k];
         v[k] = -INFINITY;
         if (j >= p.P) continue;
-        int64_t src = j;
-        if (rf) {
-            const int32_t q = __ldcs(p.anc + base + j);
-            if (q < 0 || q >= p.P) bad_anc = true;
-            else src = q;
-        }
-        const float4* xi = reinterpret_cast<const float4*>(p.x_prev + (base + src) * p.D);
-        float4* xo = reinterpret_cast<float4*>(p.x_next + (base + j) * p.D);
+        const float4* xi = reinterpret_cast<const float4*>(p.x_prev + (base + src[k]) * D);
+        float4* xo = reinterpret_cast<float4*>(p.x_next + (base + j) * D);
         float ss = 0.0f;
-        for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int g = 0; g < (GS > 0 ? GS : 16); ++g) {
+            if (GS == 0 && g >= G) break;
             const float4 x = __ldcs(xi + g);
             const float4 z = normals4((uint32_t)j, c1 + (uint32_t)g, (uint32_t)f, p.key0, p.key1);
             float4 xn;
@@ -152,8 +167,7 @@ __global__ void __launch_bounds__(kLgThreads) k_lg_step(LgParams p) {
             const float d0 = y.x - xn.x, d1 = y.y - xn.y, d2 = y.z - xn.z, d3 = y.w - xn.w;
             ss += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
         }
-        const float prev = rf ? 0.0f : p.lw[base + j];
-        const float w = prev + (p.c_obs - p.inv2r * ss);
+        const float w = prev[k] + (p.c_obs - p.inv2r * ss);
         p.lw[base + j] = w;
         if (w != w || w == INFINITY) bad_w = true;
         v[k] = w;
@@ -230,8 +244,13 @@ cudaError_t launch_lg_init(const LgParams& p, int num_sms, cudaStream_t s) {
 }
 
 cudaError_t launch_lg_step(const LgParams& p, cudaStream_t s) {
-    const int64_t blocks = (int64_t)p.F * p.n_tiles;
-    k_lg_step<<<(unsigned)blocks, kLgThreads, 0, s>>>(p);
+    const unsigned blocks = (unsigned)((int64_t)p.F * p.n_tiles);
+    switch (p.D) {
+    case 4: k_lg_step<1><<<blocks, kLgThreads, 0, s>>>(p); break;
+    case 8: k_lg_step<2><<<blocks, kLgThreads, 0, s>>>(p); break;
+    case 16: k_lg_step<4><<<blocks, kLgThreads, 0, s>>>(p); break;
+    default: k_lg_step<0><<<blocks, kLgThreads, 0, s>>>(p); break;
+    }
     return cudaGetLastError();
 }
 
