@@ -154,7 +154,9 @@ def run_gpu(args):
         # one secondary leg alone (used for profiling); prints that leg's JSON only
         hbm_peak, _ = load_peaks()
         leg = {"batched": lambda: run_batched_compare(args, pf, torch, dev, stream, hbm_peak),
-               "bootstrap": lambda: run_bootstrap(args, pf, torch, dev, hbm_peak)}[args.only]()
+               "bootstrap": lambda: run_bootstrap(args, pf, torch, dev, hbm_peak),
+               "figure2": lambda: run_figure2(args, pf, torch, dev),
+               "metropolis": lambda: run_metropolis_sweep(args, pf, torch, dev)}[args.only]()
         if rank == 0:
             print(json.dumps({"leg": args.only, **leg}))
         return
@@ -540,6 +542,113 @@ def run_bootstrap(args, pf, torch, dev, hbm_peak):
             "l2": "inputs (256 MiB of states per buffer) larger than L2"}
 
 
+def run_figure2(args, pf, torch, dev):
+    """The paper's experiment (Section 3, Figure 2) on this GPU: symmetric
+    Dirichlet(alpha) weights, alpha in {10, 1, .1, .01}, P = 256 ... 65536;
+    for each resampler the mean error sum_i (o_i/P - w_i/W)^2 over 1000
+    resamplings and the runtime of one call.  Metropolis uses B from the Eq. 5
+    bound (eps = 0.01).  The 1000 resamplings run as one batched launch of 1000
+    copies of the weight set (filter ids give independent streams); the error
+    is evaluated with torch ops on the device."""
+    import numpy as np
+
+    from paper_1202_6163_gb300 import workloads
+    s = torch.cuda.current_stream(dev)
+    stream = s.cuda_stream
+    kinds = {"multinomial": (pf.PF_MULTINOMIAL, pf.pf_resample_multinomial),
+             "stratified": (pf.PF_STRATIFIED, pf.pf_resample_stratified),
+             "systematic": (pf.PF_SYSTEMATIC, pf.pf_resample_systematic),
+             "metropolis": (pf.PF_METROPOLIS, pf.pf_resample_metropolis)}
+    R = 1000
+    rows = []
+    alphas = [10.0, 1.0, 0.1, 0.01]
+    Ps = [1 << k for k in range(8, 17)]
+    for ai, alpha in enumerate(alphas):
+        for P in Ps:
+            lw_h = workloads.dirichlet_logw(P, alpha, seed=1000 * ai + P)
+            lw = torch.from_numpy(lw_h).to(dev)
+            p64 = torch.softmax(lw.double(), 0)
+            w_max = float(p64.max())
+            B = pf.pf_metropolis_B(P, w_max, 0.01)
+            row = {"alpha": alpha, "P": P, "ess_over_P": round(float(1.0 / (p64 * p64).sum()) / P, 4),
+                   "metropolis_B": B}
+            anc1 = torch.empty(P, dtype=torch.int32, device=dev)
+            for name, (kind, fn) in kinds.items():
+                b = B if kind == pf.PF_METROPOLIS else 0
+                # runtime of one call (median of 30, back to back after 3 warm-up calls)
+                for i in range(3):
+                    fn(lw, P, b, i, anc1, stream)
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(31)]
+                for i in range(30):
+                    evs[i].record(s)
+                    fn(lw, P, b, 100 + i, anc1, stream)
+                evs[30].record(s)
+                torch.cuda.synchronize(dev)
+                us = statistics.median(evs[i].elapsed_time(evs[i + 1]) * 1e3 for i in range(30))
+                # error over resamplings: one batched launch of r copies
+                r = R
+                if kind == pf.PF_METROPOLIS:
+                    r = int(max(50, min(R, 2e11 // max(1, P * B))))  # bounded chain steps
+                lw_r = lw.repeat(r)
+                off = torch.arange(r + 1, dtype=torch.int64, device=dev) * P
+                seeds = torch.full((r,), 7 + ai, dtype=torch.int64, device=dev)
+                anc = torch.empty(r * P, dtype=torch.int32, device=dev)
+                pf.pf_resample_batched(kind, lw_r, off, r, b, seeds, anc, stream)
+                fil = torch.arange(r, device=dev, dtype=torch.int64).repeat_interleave(P)
+                o = torch.bincount(anc.long() + fil * P, minlength=r * P).view(r, P).double()
+                err = ((o / P - p64[None, :]) ** 2).sum(1)
+                torch.cuda.synchronize(dev)
+                if pf.pf_get_device_status(s) != pf.PF_OK:
+                    raise RuntimeError(f"device status not OK in figure-2 {name} P={P} alpha={alpha}")
+                row[name] = {"us": round(us, 2), "error": float(err.mean()), "resamplings": r}
+                del lw_r, anc, fil, o, err
+            rows.append(row)
+    return {"workload": "symmetric Dirichlet(alpha) weights, alpha in {10,1,.1,.01}, P = 2^8..2^16; "
+                        "error = mean over resamplings of sum_i (o_i/P - w_i/W)^2; runtime = median single call",
+            "rows": rows}
+
+
+def run_metropolis_sweep(args, pf, torch, dev):
+    """Metropolis at P = 2^20 over log-weight spreads s in {0.25, 1, 2, 4} and
+    B in {8, 32, 128, 512}: time per call, chain steps/s, and the bias each B
+    leaves (pf_metropolis_bias: the exact deviation of the probability of
+    ending on the heaviest particle) beside the B that Eq. 5 asks for eps = 0.01."""
+    import numpy as np
+
+    from paper_1202_6163_gb300 import workloads
+    s = torch.cuda.current_stream(dev)
+    stream = s.cuda_stream
+    P = 1 << 20
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    anc = torch.empty(P, dtype=torch.int32, device=dev)
+    rows = []
+    for sp in (0.25, 1.0, 2.0, 4.0):
+        lw_h = workloads.gaussian_logw(P, sp, seed=int(100 * sp))
+        lw = torch.from_numpy(lw_h).to(dev)
+        w_max = float(torch.softmax(lw.double(), 0).max())
+        row = {"s": sp, "w_max": w_max, "B_bound_eps_0.01": pf.pf_metropolis_B(P, w_max, 0.01), "by_B": {}}
+        for B in (8, 32, 128, 512):
+            for i in range(3):
+                pf.pf_resample_metropolis(lw, P, B, i, anc, stream)
+            ts = []
+            for i in range(10):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                pf.pf_resample_metropolis(lw, P, B, 10 + i, anc, stream)
+                e1.record(s)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1) * 1e3)
+            us = statistics.median(ts)
+            row["by_B"][B] = {"us": round(us, 2), "steps_per_s": round(P * B / (us * 1e-6), 1),
+                              "bias": pf.pf_metropolis_bias(P, w_max, B)}
+        rows.append(row)
+    if pf.pf_get_device_status(s) != pf.PF_OK:
+        raise RuntimeError("device status not OK in the Metropolis sweep")
+    return {"workload": "P=2^20, log-weights N(0, s^2), Metropolis B in {8,32,128,512}; L2 flushed before each call",
+            "rows": rows}
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_step_time(P, metro_chains, seed):
     """One step of the oracle over a bounded sample: the three cumulative resamplers, ESS
@@ -633,7 +742,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-bootstrap", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--only", choices=["batched", "bootstrap"], default=None,
+    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis"], default=None,
                     help="run one secondary leg alone and print its JSON (for profiling)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()

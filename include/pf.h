@@ -253,6 +253,19 @@ pf_status pf_get_device_status(void* stream, pf_status* out);
  */
 int64_t pf_metropolis_B(int64_t P, double w_max, double eps);
 
+/*
+ * Bias of a Metropolis resampling with B steps (Section 2, Eqs. 3-4; for a
+ * caller who runs fewer steps than pf_metropolis_B asks, trading bias for
+ * time, as the paper's Section 3 suggests): the largest deviation, over the
+ * chains' starting particles, of the probability of ending on the heaviest
+ * particle from w_max, max(alpha, beta)/(alpha + beta) lambda^B, which equals
+ * max(w_max, 1 - w_max) (1 - 1/(P w_max))^B.  The heaviest particle's
+ * indicator follows the two-state chain of Eq. 3 exactly, so this is the
+ * exact deviation, not only a bound.  Returns -1 for invalid arguments
+ * (P < 1, w_max outside (0, 1], B < 0).  Host-only, pure.
+ */
+double pf_metropolis_bias(int64_t P, double w_max, int64_t B);
+
 /* Human-readable name of a status code (static storage). */
 const char* pf_status_string(pf_status status);
 

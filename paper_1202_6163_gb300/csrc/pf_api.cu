@@ -337,7 +337,7 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     const int per_sm = info->batched_per_sm[kind];
     if (per_sm < 1) return PF_ERR_CUDA;
     const int grid = info->num_sms * per_sm;
-    const int64_t per_cta = kind == PF_MULTINOMIAL ? (int64_t)batched_scratch_floats_per_cta() : 0;
+    const int64_t per_cta = kind != PF_METROPOLIS ? (int64_t)batched_scratch_floats_per_cta() : 0;
     Workspace* w;
     st = workspace(s, (size_t)grid * per_cta * sizeof(float), w);
     if (st) return st;
@@ -380,9 +380,11 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
     if (red > need) need = red;
     if (F_max > 0) {
-        const size_t batched = (size_t)info->num_sms * info->batched_per_sm[PF_MULTINOMIAL] *
-                               batched_scratch_floats_per_cta() * sizeof(float);
-        if (batched > need) need = batched;
+        for (int k = PF_MULTINOMIAL; k <= PF_SYSTEMATIC; ++k) {
+            const size_t batched = (size_t)info->num_sms * info->batched_per_sm[k] *
+                                   batched_scratch_floats_per_cta() * sizeof(float);
+            if (batched > need) need = batched;
+        }
         // bootstrap-filter steps: one record per tile, one counter per filter
         const size_t lg = lg_record_bytes(F_max, (total_max + F_max - 1) / F_max) + (size_t)F_max * sizeof(float4);
         if (lg > need) need = lg;
@@ -430,6 +432,15 @@ int64_t pf_metropolis_B(int64_t P, double w_max, double eps) {
     double b = std::ceil(std::log(target) / std::log(lambda));
     if (b >= 1.0 && std::pow(lambda, b - 1.0) <= target) b -= 1.0;
     return (int64_t)b;
+}
+
+double pf_metropolis_bias(int64_t P, double w_max, int64_t B) {
+    if (P < 1 || !(w_max > 0.0) || w_max > 1.0 || B < 0) return -1.0;
+    const double beta = 1.0 / (double)P;
+    const double alpha = (1.0 - w_max) / ((double)P * w_max);
+    const double lambda = 1.0 - alpha - beta;
+    const double m = (alpha > beta ? alpha : beta) / (alpha + beta);
+    return m * std::pow(lambda > 0.0 ? lambda : 0.0, (double)B);
 }
 
 const char* pf_status_string(pf_status status) {

@@ -225,6 +225,126 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
     }
 }
 
+// Four multinomial draws (the words of one Philox block) of one filter
+// (Figure 1a).  Draw s targets u_s W (float pair); a binary search over the
+// tile table (shared memory) finds the last tile whose carry is <= the
+// target, then a lower-bound search in that tile's cumulative weights finds
+// the first element whose weight exceeds the tile-local target.  The four
+// in-tile searches advance in lockstep, so their loads overlap.
+//   table[T]  tile entries;  v  the filter's cumulative weights by tile
+//   (sign bit: zero weight; shared memory if SMEM_V, else global/L2);
+//   tile  tile length;  PA = P + lead.  Writes filter-local ancestors to a[].
+template <bool SMEM_V>
+__device__ __forceinline__ void multinomial_draws4(const u32x4& r, const TableEntry* table, int T,
+                                                   const float* v, int tile, int64_t PA, int lead, float Wh,
+                                                   float Wl, int32_t (&a)[4]) {
+    float xh[4], xl[4];
+    int lo[4], n[4], il[4];
+    int64_t b0[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        float uh, ul;
+        u32_pair(word_of(r, s), uh, ul);
+        const float th = __fmul_rn(uh, Wh);
+        const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
+        int tlo = 0, thi = T - 1;
+        while (tlo < thi) {
+            const int mid = (tlo + thi + 1) >> 1;
+            const float d = __fadd_rn(__fsub_rn(table[mid].bhi, th), __fsub_rn(table[mid].blo, tl));
+            if (d <= 0.f) tlo = mid;
+            else thi = mid - 1;
+        }
+        while (tlo > 0 && table[tlo].il < 0) --tlo;  // never settle on a tile without weight
+        const TableEntry e = table[tlo];
+        float h = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
+        float l = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
+        if (h + l < 0.f) {
+            h = 0.f;
+            l = 0.f;
+        }
+        xh[s] = h;
+        xl[s] = l;
+        b0[s] = (int64_t)tlo * tile;
+        n[s] = (int)min((int64_t)tile, PA - b0[s]);
+        lo[s] = 0;
+        il[s] = e.il;
+    }
+    const int nt[4] = {n[0], n[1], n[2], n[3]};
+    // lower bound: first i with |v_i| - xh > xl (|v| - xh is exact near the decision)
+    for (int it = 0; it < 15 && (n[0] | n[1] | n[2] | n[3]) > 0; ++it) {
+        float val[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float* q = v + b0[s] + lo[s] + (n[s] >> 1);
+            val[s] = n[s] > 0 ? (SMEM_V ? *q : __ldcg(q)) : 0.f;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (n[s] > 0) {
+                const int half = n[s] >> 1;
+                if (__fsub_rn(fabsf(val[s]), xh[s]) > xl[s]) {
+                    n[s] = half;
+                } else {
+                    lo[s] += half + 1;
+                    n[s] -= half + 1;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float* vt = v + b0[s];
+        auto ld = [&](int i) -> float { return SMEM_V ? vt[i] : __ldcg(vt + i); };
+        int idx = il[s];
+        if (lo[s] < nt[s]) {
+            idx = lo[s];
+            if (zero_flag(ld(idx))) {  // rounding landed on a zero weight: the next positive one
+                int f = il[s];
+                for (int z = idx + 1; z < nt[s]; ++z)
+                    if (!zero_flag(ld(z))) {
+                        f = z;
+                        break;
+                    }
+                idx = f;
+            }
+        }
+        a[s] = (int32_t)(b0[s] + idx - lead);
+    }
+}
+
+// Reloads a tile stored by write_tile_v into th (elements of tile-local
+// indices [0, n)): v from the magnitudes, the positive-weight mask from the
+// sign bits.  Slots at or beyond n are not read.
+__device__ __forceinline__ void read_tile_v(const float* vg0, int n, TileThread& th) {
+    const int K = per_thread_count(n);
+    th.K = K;
+    th.e0 = threadIdx.x * K;
+    const float* vg = vg0 + th.e0;
+    uint32_t pos = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxPerThread / 4; ++q) {
+        if (4 * q < K) {
+            float o[4];
+            if (th.e0 + 4 * q + 3 < n) {
+                const float4 t = __ldcg(reinterpret_cast<const float4*>(vg + 4 * q));
+                o[0] = t.x;
+                o[1] = t.y;
+                o[2] = t.z;
+                o[3] = t.w;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) o[r] = th.e0 + 4 * q + r < n ? __ldcg(vg + 4 * q + r) : -0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                th.v[4 * q + r] = fabsf(o[r]);
+                if (!zero_flag(o[r])) pos |= 1u << (4 * q + r);
+            }
+        }
+    }
+    th.pos = pos;
+}
+
 // The tile's cumulative weights to global memory (sign bit: zero weight), for the searches.
 __device__ __forceinline__ void write_tile_v(const SortedParams& p, const TileThread& th, int64_t t0, int n) {
     float* vg = p.v_out + t0 + th.e0;

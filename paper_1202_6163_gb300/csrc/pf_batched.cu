@@ -36,56 +36,6 @@ struct BatchShared {
 
 __host__ __device__ constexpr size_t batched_smem_bytes() { return sizeof(BatchShared) + kIoCap * sizeof(int32_t); }
 
-// One multinomial draw of a filter: target u W, tile search over the filter's
-// table, binary search in the tile's cumulative weights (shared or global).
-template <bool SMEM_V>
-__device__ __forceinline__ int32_t batched_draw(const SortedParams& p, const BatchShared& sm, int Tf, uint32_t x) {
-    float uh, ul;
-    u32_pair(x, uh, ul);
-    const float Wh = sm.as.W_hi, Wl = sm.as.W_lo;
-    const float th = __fmul_rn(uh, Wh);
-    const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
-    int lo = 0, hi = Tf - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        const float d = __fadd_rn(__fsub_rn(sm.table[mid].bhi, th), __fsub_rn(sm.table[mid].blo, tl));
-        if (d <= 0.f) lo = mid;
-        else hi = mid - 1;
-    }
-    int tt = lo;
-    while (tt > 0 && sm.table[tt].il < 0) --tt;
-    const TableEntry e = sm.table[tt];
-    float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
-    float xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
-    if (xh + xl < 0.f) {
-        xh = 0.f;
-        xl = 0.f;
-    }
-    const int64_t b0 = (int64_t)tt * kTileMax;
-    const int nt = (int)min((int64_t)kTileMax, p.P + p.lead - b0);
-    const float* vt = p.v_out + b0;
-    auto ld = [&](int i) -> float { return SMEM_V ? vt[i] : __ldcg(vt + i); };
-    int l2 = 0, h2 = nt;
-    while (l2 < h2) {
-        const int mid = (l2 + h2) >> 1;
-        if (__fsub_rn(fabsf(ld(mid)), xh) > xl) h2 = mid;
-        else l2 = mid + 1;
-    }
-    int idx = e.il;
-    if (l2 < nt) {
-        idx = l2;
-        if (zero_flag(ld(idx))) {
-            int f = e.il;
-            for (int z = idx + 1; z < nt; ++z)
-                if (!zero_flag(ld(z))) {
-                    f = z;
-                    break;
-                }
-            idx = f;
-        }
-    }
-    return (int32_t)(b0 + idx - p.lead);
-}
 
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
@@ -132,9 +82,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
         p.wait_ns = 0;
         p.skip_tile = -1;
         p.lead = lead;
-        p.v_out = (KIND == KIND_MULTI)
-                      ? (Tf == 1 ? reinterpret_cast<float*>(region) : bp.scratch + (int64_t)blockIdx.x * bp.scratch_per_cta)
-                      : nullptr;
+        // cumulative weights of the filter's tiles: multinomial searches them;
+        // systematic and stratified reload them in pass 2 instead of rescanning
+        p.v_out = (KIND == KIND_MULTI && Tf == 1) ? reinterpret_cast<float*>(region)
+                  : (Tf > 1 ? bp.scratch + (int64_t)blockIdx.x * bp.scratch_per_cta : nullptr);
 
         // pass 1: scan and record the filter's tiles
         TileSummary ts;
@@ -150,7 +101,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                 sm.rsl[c] = ts.S.lo;
                 sm.ril[c] = ts.i_last;
             }
-            if (KIND == KIND_MULTI) write_tile_v(p, th, t0, n);
+            if (KIND == KIND_MULTI || c < Tf - 1) {
+                if (p.v_out) write_tile_v(p, th, t0, n);
+            }
             __syncthreads();
         }
         // carries of the filter's tiles (warp 0, one tile per lane)
@@ -191,13 +144,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
             const int64_t nq = (Pf + 3) >> 2;  // four draws per Philox block
             for (int64_t q = tid; q < nq; q += kThreads) {
                 const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
+                int32_t a[4];
+                if (Tf == 1)
+                    multinomial_draws4<true>(r, sm.table, Tf, p.v_out, kTileMax, PA, lead, sm.as.W_hi, sm.as.W_lo, a);
+                else
+                    multinomial_draws4<false>(r, sm.table, Tf, p.v_out, kTileMax, PA, lead, sm.as.W_hi, sm.as.W_lo,
+                                              a);
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    const int64_t j = 4 * q + s;
-                    if (j < Pf)
-                        p.anc[j] = Tf == 1 ? batched_draw<true>(p, sm, Tf, word_of(r, s))
-                                           : batched_draw<false>(p, sm, Tf, word_of(r, s));
-                }
+                for (int s = 0; s < 4; ++s)
+                    if (4 * q + s < Pf) p.anc[4 * q + s] = a[s];
             }
             __syncthreads();
             continue;
@@ -206,7 +161,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
         int32_t* out = reinterpret_cast<int32_t*>(region);
         for (int c = Tf - 1; c >= 0; --c) {
             const int64_t t0 = (int64_t)c * kTileMax;
-            if (c != Tf - 1) ts = tile_scan(p.lw + t0, c == 0 ? lead : 0, (int)min((int64_t)kTileMax, PA - t0), sm.tile, th);
+            if (c != Tf - 1) {
+                read_tile_v(p.v_out + t0, (int)min((int64_t)kTileMax, PA - t0), th);
+                ts.k = sm.rk[c];
+                ts.i_last = sm.ril[c];
+            }
             if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
             __syncthreads();
             assign_offspring<KIND>(p, sm.as, out, th, ts, t0 - lead);

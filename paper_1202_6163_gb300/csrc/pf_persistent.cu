@@ -157,56 +157,7 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
     for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
         const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
         int32_t a[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            float uh, ul;
-            u32_pair(word_of(r, s), uh, ul);
-            // target u W as a float pair
-            const float th = __fmul_rn(uh, Wh);
-            const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
-            // last tile whose carry is <= the target (compared by value)
-            int lo = 0, hi = T - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                const float d = __fadd_rn(__fsub_rn(table[mid].bhi, th), __fsub_rn(table[mid].blo, tl));
-                if (d <= 0.f) lo = mid;
-                else hi = mid - 1;
-            }
-            int tt = lo;
-            while (tt > 0 && table[tt].il < 0) --tt;  // never settle on a tile without weight
-            const TableEntry e = table[tt];
-            // tile-local target as a pair (exact binary scaling)
-            float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
-            float xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
-            if (xh + xl < 0.f) {
-                xh = 0.f;
-                xl = 0.f;
-            }
-            const int64_t b0 = (int64_t)tt * p.tile;
-            const int nt = (int)min((int64_t)p.tile, p.P + p.lead - b0);
-            const float* vt = p.v_out + b0;
-            int l2 = 0, h2 = nt;
-            while (l2 < h2) {
-                const int mid = (l2 + h2) >> 1;
-                // |v| > xh + xl, with |v| - xh exact near the decision
-                if (__fsub_rn(fabsf(__ldcg(vt + mid)), xh) > xl) h2 = mid;
-                else l2 = mid + 1;
-            }
-            int idx = e.il;
-            if (l2 < nt) {
-                idx = l2;
-                if (zero_flag(__ldcg(vt + idx))) {
-                    int f = e.il;
-                    for (int z = idx + 1; z < nt; ++z)
-                        if (!zero_flag(__ldcg(vt + z))) {
-                            f = z;
-                            break;
-                        }
-                    idx = f;
-                }
-            }
-            a[s] = (int32_t)(b0 + idx - p.lead);
-        }
+        multinomial_draws4<false>(r, table, T, p.v_out, p.tile, p.P + p.lead, p.lead, Wh, Wl, a);
         const int64_t j = 4 * q;
         if (j + 3 < p.P && (((uintptr_t)(p.anc + j)) & 15u) == 0) {
             *reinterpret_cast<int4*>(p.anc + j) = make_int4(a[0], a[1], a[2], a[3]);

@@ -69,3 +69,27 @@ def test_host_only_entry_points(lib):
         assert pf.pf_metropolis_B(P, w, eps) == oracle.metropolis_B(P, w, eps)
     assert pf.pf_metropolis_B(0, 0.5, 0.01) == -1
     assert pf.pf_metropolis_B(10, 0.0, 0.01) == -1
+
+
+def test_metropolis_bias_is_the_exact_chain_deviation(lib):
+    # host-only: the deviation max_i |(M^B)[i, p_max] - w_max| of the exact
+    # transition matrix equals the closed form for every B, and the bound's B
+    # is the first with deviation <= eps
+    from paper_1202_6163_gb300 import pf
+    for lw in ([0.0, -0.5, 1.2, -2.0, 0.3], [0.0, 0.0, 0.0, 1.5], [2.0, -1.0, -1.0, -1.0, -1.0, 0.5]):
+        lw = np.array(lw, np.float32)
+        P = lw.size
+        w = np.exp(lw.astype(np.float64) - lw.max())
+        w_max = w.max() / w.sum()
+        M = oracle.metropolis_matrix(lw)
+        pmax = int(np.argmax(lw))
+        MB = np.eye(P)
+        for B in range(40):
+            dev = np.abs(MB[:, pmax] - w_max).max()
+            assert pf.pf_metropolis_bias(P, w_max, B) == pytest.approx(dev, rel=1e-9, abs=1e-15)
+            MB = MB @ M
+        for eps in (0.1, 0.01, 0.001):
+            B = pf.pf_metropolis_B(P, w_max, eps)
+            assert pf.pf_metropolis_bias(P, w_max, B) <= eps * (1 + 1e-12)
+            assert B == 0 or pf.pf_metropolis_bias(P, w_max, B - 1) > eps
+    assert pf.pf_metropolis_bias(0, 0.5, 3) == -1 and pf.pf_metropolis_bias(10, 0.5, -1) == -1
