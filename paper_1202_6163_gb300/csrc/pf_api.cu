@@ -338,9 +338,16 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     if (per_sm < 1) return PF_ERR_CUDA;
     const int grid = info->num_sms * per_sm;
     const int64_t per_cta = kind != PF_METROPOLIS ? (int64_t)batched_scratch_floats_per_cta() : 0;
+    const size_t order_at = ((size_t)grid * per_cta * sizeof(float) + 255) & ~(size_t)255;
+    const bool ordered = F >= kOrderMinF && F <= kOrderMaxF;
     Workspace* w;
-    st = workspace(s, (size_t)grid * per_cta * sizeof(float), w);
+    st = workspace(s, order_at + (ordered ? (size_t)F * sizeof(int32_t) : 0), w);
     if (st) return st;
+    int32_t* order = ordered ? reinterpret_cast<int32_t*>((char*)w->scratch + order_at) : nullptr;
+    if (order) {
+        const cudaError_t e = launch_batched_order(offsets, F, order, s);
+        if (e != cudaSuccess) return cuda_fail(e, "batched order launch");
+    }
     BatchParams bp;
     bp.lw = logw;
     bp.offsets = offsets;
@@ -352,6 +359,7 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     bp.scratch = (float*)w->scratch;
     bp.scratch_per_cta = per_cta;
     bp.mask = mask;
+    bp.order = order;
     if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
     return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
 }
@@ -380,9 +388,11 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
     if (red > need) need = red;
     if (F_max > 0) {
-        for (int k = PF_MULTINOMIAL; k <= PF_SYSTEMATIC; ++k) {
-            const size_t batched = (size_t)info->num_sms * info->batched_per_sm[k] *
-                                   batched_scratch_floats_per_cta() * sizeof(float);
+        for (int k = PF_MULTINOMIAL; k <= PF_METROPOLIS; ++k) {
+            const size_t per_cta = k != PF_METROPOLIS ? batched_scratch_floats_per_cta() : 0;
+            const size_t order_at = ((size_t)info->num_sms * info->batched_per_sm[k] * per_cta * sizeof(float) + 255) &
+                                    ~(size_t)255;
+            const size_t batched = order_at + (size_t)F_max * sizeof(int32_t);
             if (batched > need) need = batched;
         }
         // bootstrap-filter steps: one record per tile, one counter per filter

@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
     for (;;) {
         if (tid == 0) sm.f = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
         __syncthreads();
-        const int f = sm.f;
+        const int ticket = sm.f;
         __syncthreads();
-        if (f >= bp.F) break;
+        if (ticket >= bp.F) break;
+        const int f = bp.order ? bp.order[ticket] : ticket;
         if (bp.mask && bp.mask[f] == 0) continue;
         const int64_t off0 = bp.offsets[f], off1 = bp.offsets[f + 1];
         const int64_t Pf = off1 - off0;
@@ -206,6 +207,39 @@ int batched_blocks_per_sm(int kind) {
 }
 
 size_t batched_scratch_floats_per_cta() { return (size_t)kMaxOwnB * kTileMax; }
+
+// One CTA: a counting sort of the filters by tile count, largest first (the
+// order within a class is whatever the shared-memory atomics give; each
+// filter's result does not depend on it).
+constexpr int kOrderThreads = 1024;
+__global__ void __launch_bounds__(kOrderThreads) k_batched_order(const int64_t* __restrict__ offsets, int F,
+                                                                 int32_t* __restrict__ order) {
+    __shared__ int start[kMaxOwnB + 2];
+    const int tid = threadIdx.x;
+    if (tid < kMaxOwnB + 2) start[tid] = 0;
+    __syncthreads();
+    auto cls = [&](int f) {
+        const int64_t n = offsets[f + 1] - offsets[f];
+        return n <= 0 ? 0 : (int)min((int64_t)kMaxOwnB + 1, (n + kTileMax - 1) / kTileMax);
+    };
+    for (int f = tid; f < F; f += kOrderThreads) atomicAdd(&start[cls(f)], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int c = kMaxOwnB + 1; c >= 0; --c) {
+            const int n = start[c];
+            start[c] = run;
+            run += n;
+        }
+    }
+    __syncthreads();
+    for (int f = tid; f < F; f += kOrderThreads) order[atomicAdd(&start[cls(f)], 1)] = f;
+}
+
+cudaError_t launch_batched_order(const int64_t* offsets, int F, int32_t* order, cudaStream_t s) {
+    k_batched_order<<<1, kOrderThreads, 0, s>>>(offsets, F, order);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s) {
     const size_t smem = batched_smem_bytes();

@@ -75,7 +75,13 @@ struct BatchParams {
     float* scratch;           // multinomial: per-CTA cumulative weights of multi-tile filters
     int64_t scratch_per_cta;  // floats per CTA
     const int32_t* mask;      // optional: filters with mask[f] == 0 are skipped
+    const int32_t* order;     // optional: ticket t resamples filter order[t] (largest first)
 };
+
+// Filters of a batched call ordered by decreasing size, so that the largest
+// are taken first and the persistent grid does not end on one long filter.
+constexpr int kOrderMinF = 64;        // fewer filters: natural order
+constexpr int kOrderMaxF = 1 << 20;   // more filters: natural order (one-CTA ordering pass)
 
 // One step of F bootstrap filters on the linear-Gaussian test model.
 struct LgParams {
@@ -113,6 +119,7 @@ cudaError_t launch_lg_init(const LgParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_lg_step(const LgParams& p, cudaStream_t s);
 int persistent_blocks_per_sm(int kind);
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s);
+cudaError_t launch_batched_order(const int64_t* offsets, int F, int32_t* order, cudaStream_t s);
 int batched_blocks_per_sm(int kind);
 size_t batched_scratch_floats_per_cta();
 cudaError_t launch_batched_metropolis(const BatchParams& bp, int grid, cudaStream_t s);

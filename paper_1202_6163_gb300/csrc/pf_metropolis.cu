@@ -126,9 +126,10 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
     for (;;) {
         if (tid == 0) f_sm = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
         __syncthreads();
-        const int f = f_sm;
+        const int ticket = f_sm;
         __syncthreads();
-        if (f >= bp.F) break;
+        if (ticket >= bp.F) break;
+        const int f = bp.order ? bp.order[ticket] : ticket;
         if (bp.mask && bp.mask[f] == 0) continue;
         const int64_t off0 = bp.offsets[f], off1 = bp.offsets[f + 1];
         const int64_t Pf = off1 - off0;
