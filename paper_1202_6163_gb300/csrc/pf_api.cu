@@ -337,17 +337,21 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     const int per_sm = info->batched_per_sm[kind];
     if (per_sm < 1) return PF_ERR_CUDA;
     const int grid = info->num_sms * per_sm;
-    const int64_t per_cta = kind != PF_METROPOLIS ? (int64_t)batched_scratch_floats_per_cta() : 0;
-    const size_t order_at = ((size_t)grid * per_cta * sizeof(float) + 255) & ~(size_t)255;
-    const bool ordered = F >= kOrderMinF && F <= kOrderMaxF;
+    // scratch: per-CTA cumulative weights (multinomial), the plan's items, the
+    // split filters' tile records; two counters per filter
+    const int64_t per_cta = kind == PF_MULTINOMIAL ? (int64_t)batched_scratch_floats_per_cta() : 0;
+    const size_t items_at = ((size_t)grid * per_cta * sizeof(float) + 255) & ~(size_t)255;
+    const size_t n_items = (size_t)F * kMaxItemsPerFilter;
+    const size_t records_at = (items_at + n_items * sizeof(int32_t) + 255) & ~(size_t)255;
     Workspace* w;
-    st = workspace(s, order_at + (ordered ? (size_t)F * sizeof(int32_t) : 0), w);
+    st = workspace(s, records_at + n_items * sizeof(uint4), w);
     if (st) return st;
-    int32_t* order = ordered ? reinterpret_cast<int32_t*>((char*)w->scratch + order_at) : nullptr;
-    if (order) {
-        const cudaError_t e = launch_batched_order(offsets, F, order, s);
-        if (e != cudaSuccess) return cuda_fail(e, "batched order launch");
-    }
+    st = ensure_counters(*w, 2 * (size_t)F, s);
+    if (st) return st;
+    int32_t* items = reinterpret_cast<int32_t*>((char*)w->scratch + items_at);
+    const int split = kind == PF_STRATIFIED || kind == PF_SYSTEMATIC;
+    cudaError_t e = launch_batched_plan(logw, offsets, F, mask, split, items, w->ctl, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched plan launch");
     BatchParams bp;
     bp.lw = logw;
     bp.offsets = offsets;
@@ -358,8 +362,10 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     bp.ctl = w->ctl;
     bp.scratch = (float*)w->scratch;
     bp.scratch_per_cta = per_cta;
-    bp.mask = mask;
-    bp.order = order;
+    bp.items = items;
+    bp.records = reinterpret_cast<uint4*>((char*)w->scratch + records_at);
+    bp.counters = w->counters;
+    bp.wait_ns = g_wait_ns;
     if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
     return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
 }
@@ -389,10 +395,11 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     if (red > need) need = red;
     if (F_max > 0) {
         for (int k = PF_MULTINOMIAL; k <= PF_METROPOLIS; ++k) {
-            const size_t per_cta = k != PF_METROPOLIS ? batched_scratch_floats_per_cta() : 0;
-            const size_t order_at = ((size_t)info->num_sms * info->batched_per_sm[k] * per_cta * sizeof(float) + 255) &
-                                    ~(size_t)255;
-            const size_t batched = order_at + (size_t)F_max * sizeof(int32_t);
+            const size_t per_cta = k == PF_MULTINOMIAL ? batched_scratch_floats_per_cta() : 0;
+            const size_t items_at =
+                ((size_t)info->num_sms * info->batched_per_sm[k] * per_cta * sizeof(float) + 255) & ~(size_t)255;
+            const size_t n_items = (size_t)F_max * kMaxItemsPerFilter;
+            const size_t batched = ((items_at + n_items * sizeof(int32_t) + 255) & ~(size_t)255) + n_items * sizeof(uint4);
             if (batched > need) need = batched;
         }
         // bootstrap-filter steps: one record per tile, one counter per filter
@@ -403,7 +410,7 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     st = workspace(s, need, w);
     if (st) return st;
     if (F_max > 0) {
-        st = ensure_counters(*w, (size_t)F_max, s);
+        st = ensure_counters(*w, 2 * (size_t)F_max, s);
         if (st) return st;
     }
     return cuda_fail(cudaStreamSynchronize(s), "cudaStreamSynchronize");

@@ -1,14 +1,26 @@
 // Batched resampling of many independent filters in one launch (the many
 // filters of particle MCMC, Section 1): cumulative schemes.
 //
-// A persistent grid takes filters from a ticket counter.  One CTA resamples a
-// whole filter -- at most kMaxOwnB tiles -- so no CTA ever waits on another:
-// pass 1 scans and records each tile (pf_tile.cuh); warp 0 forms the tiles'
-// exact fixed-point carries; pass 2 assigns offsets tile by tile
-// (systematic, stratified) or the CTA draws the filter's uniforms and
-// searches its tiles (multinomial).  A filter's data may start at any 4-byte
-// boundary: tiles are laid out on the aligned window, with the leading slots
-// taken as zero weights.  The last CTA to finish resets the ticket.
+// A one-CTA plan pass turns the filters into a list of work items, largest
+// filters first (a counting sort by tile count), skipping masked and empty
+// filters.  A persistent grid then takes items from a ticket counter:
+//   - a filter of one tile (or any multinomial filter) is one item, done by
+//     one CTA with no wait on any other: scan and record each tile
+//     (pf_tile.cuh), warp 0 forms the tiles' exact fixed-point carries, then
+//     offsets are assigned (systematic, stratified) or the filter's uniforms
+//     drawn and searched (multinomial);
+//   - a systematic or stratified filter of Tf > 1 tiles is Tf items with
+//     consecutive tickets, one tile each: every CTA scans its tile in
+//     registers, publishes a 16-byte record, waits (bounded) until all Tf
+//     records of its filter are in, forms the same carries from them and
+//     assigns its own tile's offsets.  Tiles of one filter hold consecutive
+//     tickets and a filter has at most kMaxOwnB < grid tiles, so every tile a
+//     CTA waits for has been or will be taken by a running CTA (the launch is
+//     cooperative, so all CTAs are resident).
+// A filter's data may start at any 4-byte boundary: tiles are laid out on the
+// aligned window, with the leading slots taken as zero weights.  The last CTA
+// to finish resets the ticket; the last CTA of a split filter resets its
+// arrival counters.
 #include <climits>
 
 #include "pf.h"
@@ -19,6 +31,9 @@ namespace pf {
 
 constexpr int kMaxOwnB = 16;  // tiles per filter: P_f + lead <= 16 * kTileMax
 static_assert(PF_MAX_BATCHED_FILTER == (long long)kMaxOwnB * kTileMax, "batched filter capacity");
+static_assert(kMaxOwnB <= 31, "the carries give one tile to each lane of warp 0; item codes use 5 bits");
+static_assert(kMaxOwnB == kMaxItemsPerFilter, "items per filter");
+constexpr int kWhole = 31;  // item code: the whole filter in one CTA
 
 struct BatchShared {
     TileShared tile;
@@ -37,57 +52,154 @@ struct BatchShared {
 __host__ __device__ constexpr size_t batched_smem_bytes() { return sizeof(BatchShared) + kIoCap * sizeof(int32_t); }
 
 
+// The filter's geometry and parameters for the tile routines.
+__device__ __forceinline__ void filter_params(const BatchParams& bp, int f, int64_t off0, int64_t Pf, int lead, int Tf,
+                                              SortedParams& p) {
+    p.lw = bp.lw + off0 - lead;
+    p.anc = bp.anc + off0;
+    p.P = Pf;
+    p.Pd = (double)Pf;
+    p.tile = kTileMax;
+    p.n_tiles = Tf;
+    p.tiles_per_cta = Tf;
+    const uint64_t seed = bp.seeds[f];
+    p.key0 = (uint32_t)(seed & 0xffffffffu);
+    p.key1 = (uint32_t)(seed >> 32);
+    p.filter = (uint32_t)f;
+    p.ctl = bp.ctl;
+    p.slots = nullptr;
+    p.wait_ns = 0;
+    p.skip_tile = -1;
+    p.lead = lead;
+    p.v_out = nullptr;
+}
+
+// Warp 0: the exact fixed-point carries of a filter's Tf tiles from their
+// records (lane t holds tile t's exponent, sum and last positive element)
+// into sm.Bown / sm.as (and the multinomial tile table); sm.skip = 1 (and
+// PF_ERR_DOMAIN from `report`) when a tile saw NaN/+inf or all weights are zero.
+template <int KIND>
+__device__ __forceinline__ void filter_carries(BatchShared& sm, const BatchParams& bp, int Tf, int lane, int k,
+                                               float shi, float slo, int il, int bad, bool report) {
+    int kmax = (lane < Tf && shi > 0.f) ? k : INT_MIN;
+    kmax = warp_max_i(kmax);
+    bad = __any_sync(0xffffffffu, lane < Tf && bad);
+    const int skip = (kmax == INT_MIN || bad) ? 1 : 0;
+    if (lane == 0) {
+        sm.skip = skip;
+        if (skip && report) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
+    }
+    if (skip) return;
+    const int sh = lane < Tf ? k - kmax : 0;
+    const i128 a = lane < Tf ? fixed_of(shi, sh) + fixed_of(slo, sh) : (i128)0;
+    const i128 inc = warp_scan_i128(a, lane);
+    const i128 B = inc - a;
+    if (lane < Tf) {
+        sm.Bown[lane] = B;
+        if (KIND == KIND_MULTI) {
+            const fpair b = fixed_to_pair(B);
+            sm.table[lane] = {b.hi, b.lo, pow2f(-sh), il};
+        }
+    }
+    if (lane == 31) {
+        sm.Bown[Tf] = inc;
+        sm.as.Wt = inc;
+        sm.as.K = kmax;
+        const fpair Wp = fixed_to_pair(inc);
+        sm.as.W_hi = Wp.hi;
+        sm.as.W_lo = Wp.lo;
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BatchShared& sm = *reinterpret_cast<BatchShared*>(smem_raw);
     unsigned char* region = smem_raw + sizeof(BatchShared);
     const int tid = threadIdx.x, lane = tid & 31;
+    const int n_items = (int)ld_relaxed_u32(bp.ctl + CTL_ITEMS);
     TileThread th;
     for (;;) {
         if (tid == 0) sm.f = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
         __syncthreads();
         const int ticket = sm.f;
         __syncthreads();
-        if (ticket >= bp.F) break;
-        const int f = bp.order ? bp.order[ticket] : ticket;
-        if (bp.mask && bp.mask[f] == 0) continue;
-        const int64_t off0 = bp.offsets[f], off1 = bp.offsets[f + 1];
-        const int64_t Pf = off1 - off0;
-        if (Pf <= 0) {
-            if (Pf < 0 && tid == 0) set_status(bp.ctl + CTL_STATUS, ST_INVALID);
-            continue;
-        }
-        const float* lwf = bp.lw + off0;
-        const int lead = (int)(((uintptr_t)lwf >> 2) & 3u);
+        if (ticket >= n_items) break;
+        const int item = bp.items[ticket];
+        const int f = item >> 5, c_item = item & 31;
+        const int64_t off0 = bp.offsets[f];
+        const int64_t Pf = bp.offsets[f + 1] - off0;
+        const int lead = (int)(((uintptr_t)(bp.lw + off0) >> 2) & 3u);
         const int64_t PA = Pf + lead;
         const int Tf = (int)((PA + kTileMax - 1) / kTileMax);
-        if (Tf > kMaxOwnB) {
-            if (tid == 0) set_status(bp.ctl + CTL_STATUS, ST_INVALID);
+        SortedParams p;
+        filter_params(bp, f, off0, Pf, lead, Tf, p);
+        int32_t* out = reinterpret_cast<int32_t*>(region);
+
+        if (KIND != KIND_MULTI) {
+            // ---- systematic / stratified: one tile (a one-tile filter is its own item) ----
+            const int c = c_item == kWhole ? 0 : c_item;
+            const int64_t t0 = (int64_t)c * kTileMax;
+            TileSummary ts = tile_scan(p.lw + t0, c == 0 ? lead : 0, (int)min((int64_t)kTileMax, PA - t0), sm.tile, th);
+            uint32_t* rec = reinterpret_cast<uint32_t*>(bp.records + (ticket - c));  // the filter's Tf records
+            uint32_t* arrive = bp.counters + 2 * f;
+            if (tid == 0) {
+                int ok = 1;
+                if (Tf > 1) {
+                    st_v4_u32(rec + 4 * c, (uint32_t)ts.k, __float_as_uint(ts.S.hi), __float_as_uint(ts.S.lo),
+                              (uint32_t)(ts.i_last + 1) | (ts.bad ? 0x80000000u : 0u));
+                    __threadfence();
+                    red_release_add_u32(arrive, 1u);
+                    const uint64_t t_start = global_ns();
+                    for (uint32_t it = 1; ld_acquire_u32(arrive) < (uint32_t)Tf; ++it) {
+                        if ((it & 7u) == 0u && global_ns() - t_start > bp.wait_ns) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    if (!ok) set_status(bp.ctl + CTL_STATUS, ST_TIMEOUT);
+                } else {
+                    sm.rk[0] = ts.k;
+                    sm.rsh[0] = ts.S.hi;
+                    sm.rsl[0] = ts.S.lo;
+                    sm.ril[0] = ts.i_last;
+                }
+                sm.skip = !ok;
+            }
+            __syncthreads();
+            if (!sm.skip) {
+                if (tid < 32) {
+                    uint4 r = make_uint4(0, 0, 0, 0);
+                    if (Tf > 1) {
+                        if (lane < Tf) r = ld_cg_v4_u32(rec + 4 * lane);
+                    } else if (lane == 0) {
+                        r = make_uint4((uint32_t)sm.rk[0], __float_as_uint(sm.rsh[0]), __float_as_uint(sm.rsl[0]),
+                                       (uint32_t)(sm.ril[0] + 1) | (ts.bad ? 0x80000000u : 0u));
+                    }
+                    filter_carries<KIND>(sm, bp, Tf, lane, (int)r.x, __uint_as_float(r.y), __uint_as_float(r.z),
+                                         (int)(r.w & 0x7fffffffu) - 1, (int)(r.w >> 31), c == 0);
+                }
+                __syncthreads();
+                if (!sm.skip) {
+                    if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
+                    __syncthreads();
+                    assign_offspring<KIND>(p, sm.as, out, th, ts, t0 - lead);
+                }
+            }
+            // the last of a split filter's CTAs to leave resets its counters
+            if (Tf > 1 && tid == 0 && atomicAdd(bp.counters + 2 * f + 1, 1u) == (uint32_t)Tf - 1u) {
+                atomicExch(arrive, 0u);
+                atomicExch(bp.counters + 2 * f + 1, 0u);
+            }
+            __syncthreads();
             continue;
         }
-        SortedParams p;
-        p.lw = lwf - lead;
-        p.anc = bp.anc + off0;
-        p.P = Pf;
-        p.Pd = (double)Pf;
-        p.tile = kTileMax;
-        p.n_tiles = Tf;
-        p.tiles_per_cta = Tf;
-        const uint64_t seed = bp.seeds[f];
-        p.key0 = (uint32_t)(seed & 0xffffffffu);
-        p.key1 = (uint32_t)(seed >> 32);
-        p.filter = (uint32_t)f;
-        p.ctl = bp.ctl;
-        p.slots = nullptr;
-        p.wait_ns = 0;
-        p.skip_tile = -1;
-        p.lead = lead;
-        // cumulative weights of the filter's tiles: multinomial searches them;
-        // systematic and stratified reload them in pass 2 instead of rescanning
-        p.v_out = (KIND == KIND_MULTI && Tf == 1) ? reinterpret_cast<float*>(region)
-                  : (Tf > 1 ? bp.scratch + (int64_t)blockIdx.x * bp.scratch_per_cta : nullptr);
 
+        // ---- a whole filter in this CTA ----
+        // cumulative weights of the filter's tiles: multinomial searches them
+        if (KIND == KIND_MULTI)
+            p.v_out = Tf == 1 ? reinterpret_cast<float*>(region) : bp.scratch + (int64_t)blockIdx.x * bp.scratch_per_cta;
         // pass 1: scan and record the filter's tiles
         TileSummary ts;
         int bad = 0;
@@ -102,41 +214,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                 sm.rsl[c] = ts.S.lo;
                 sm.ril[c] = ts.i_last;
             }
-            if (KIND == KIND_MULTI || c < Tf - 1) {
-                if (p.v_out) write_tile_v(p, th, t0, n);
-            }
+            if (KIND == KIND_MULTI) write_tile_v(p, th, t0, n);
             __syncthreads();
         }
-        // carries of the filter's tiles (warp 0, one tile per lane)
         if (tid < 32) {
-            int kmax = (lane < Tf && sm.rsh[lane] > 0.f) ? sm.rk[lane] : INT_MIN;
-            kmax = warp_max_i(kmax);
-            const int skip = (kmax == INT_MIN || bad) ? 1 : 0;
-            if (lane == 0) {
-                sm.skip = skip;
-                if (skip) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
-            }
-            if (!skip) {
-                const int sh = lane < Tf ? sm.rk[lane] - kmax : 0;
-                const i128 a = lane < Tf ? fixed_of(sm.rsh[lane], sh) + fixed_of(sm.rsl[lane], sh) : (i128)0;
-                const i128 inc = warp_scan_i128(a, lane);
-                const i128 B = inc - a;
-                if (lane < Tf) {
-                    sm.Bown[lane] = B;
-                    if (KIND == KIND_MULTI) {
-                        const fpair b = fixed_to_pair(B);
-                        sm.table[lane] = {b.hi, b.lo, pow2f(-sh), sm.ril[lane]};
-                    }
-                }
-                if (lane == 31) {
-                    sm.Bown[Tf] = inc;
-                    sm.as.Wt = inc;
-                    sm.as.K = kmax;
-                    const fpair Wp = fixed_to_pair(inc);
-                    sm.as.W_hi = Wp.hi;
-                    sm.as.W_lo = Wp.lo;
-                }
-            }
+            const bool in = lane < Tf;
+            filter_carries<KIND>(sm, bp, Tf, lane, in ? sm.rk[lane] : 0, in ? sm.rsh[lane] : 0.f,
+                                 in ? sm.rsl[lane] : 0.f, in ? sm.ril[lane] : -1, bad, true);
         }
         __syncthreads();
         if (sm.skip) continue;
@@ -157,19 +241,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
             }
             __syncthreads();
             continue;
-        }
-        // pass 2: offsets tile by tile (the last tile's scan is still in registers)
-        int32_t* out = reinterpret_cast<int32_t*>(region);
-        for (int c = Tf - 1; c >= 0; --c) {
-            const int64_t t0 = (int64_t)c * kTileMax;
-            if (c != Tf - 1) {
-                read_tile_v(p.v_out + t0, (int)min((int64_t)kTileMax, PA - t0), th);
-                ts.k = sm.rk[c];
-                ts.i_last = sm.ril[c];
-            }
-            if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
-            __syncthreads();
-            assign_offspring<KIND>(p, sm.as, out, th, ts, t0 - lead);
         }
     }
     // every CTA has drawn a ticket past the end: the last one to leave resets the queue
@@ -208,48 +279,93 @@ int batched_blocks_per_sm(int kind) {
 
 size_t batched_scratch_floats_per_cta() { return (size_t)kMaxOwnB * kTileMax; }
 
-// One CTA: a counting sort of the filters by tile count, largest first (the
-// order within a class is whatever the shared-memory atomics give; each
-// filter's result does not depend on it).
-constexpr int kOrderThreads = 1024;
-__global__ void __launch_bounds__(kOrderThreads) k_batched_order(const int64_t* __restrict__ offsets, int F,
-                                                                 int32_t* __restrict__ order) {
-    __shared__ int start[kMaxOwnB + 2];
+// The plan: one CTA sorts the filters by tile count, largest first (a
+// counting sort; the order within a class is whatever the shared-memory
+// atomics give, and no filter's result depends on it) and writes the items
+// f * 32 + c (tile c of a split filter) or f * 32 + kWhole.  Masked and empty
+// filters get no item; a negative size or a filter beyond kMaxOwnB tiles sets
+// PF_ERR_INVALID and gets none.  The item count goes to ctl[CTL_ITEMS].
+constexpr int kPlanThreads = 1024;
+__global__ void __launch_bounds__(kPlanThreads) k_batched_plan(const float* __restrict__ lw,
+                                                               const int64_t* __restrict__ offsets, int F,
+                                                               const int32_t* __restrict__ mask, int split,
+                                                               int32_t* __restrict__ items, uint32_t* ctl) {
+    __shared__ int count[kMaxOwnB + 1], start[kMaxOwnB + 1];
     const int tid = threadIdx.x;
-    if (tid < kMaxOwnB + 2) start[tid] = 0;
+    if (tid <= kMaxOwnB) count[tid] = 0;
     __syncthreads();
-    auto cls = [&](int f) {
-        const int64_t n = offsets[f + 1] - offsets[f];
-        return n <= 0 ? 0 : (int)min((int64_t)kMaxOwnB + 1, (n + kTileMax - 1) / kTileMax);
+    auto tiles = [&](int f) -> int {  // 0: no item
+        if (mask && mask[f] == 0) return 0;
+        const int64_t off0 = offsets[f], n = offsets[f + 1] - off0;
+        if (n <= 0) {
+            if (n < 0) set_status(ctl + CTL_STATUS, ST_INVALID);
+            return 0;
+        }
+        const int lead = (int)(((uintptr_t)(lw + off0) >> 2) & 3u);
+        const int64_t T = (n + lead + kTileMax - 1) / kTileMax;
+        if (T > kMaxOwnB) {
+            set_status(ctl + CTL_STATUS, ST_INVALID);
+            return 0;
+        }
+        return (int)T;
     };
-    for (int f = tid; f < F; f += kOrderThreads) atomicAdd(&start[cls(f)], 1);
+    for (int f = tid; f < F; f += kPlanThreads) {
+        const int T = tiles(f);
+        if (T) atomicAdd(&count[T], 1);
+    }
     __syncthreads();
     if (tid == 0) {
         int run = 0;
-        for (int c = kMaxOwnB + 1; c >= 0; --c) {
-            const int n = start[c];
-            start[c] = run;
-            run += n;
+        for (int T = kMaxOwnB; T >= 1; --T) {
+            start[T] = run;
+            run += count[T] * (split && T > 1 ? T : 1);
         }
+        ctl[CTL_ITEMS] = (uint32_t)run;
     }
     __syncthreads();
-    for (int f = tid; f < F; f += kOrderThreads) order[atomicAdd(&start[cls(f)], 1)] = f;
+    for (int f = tid; f < F; f += kPlanThreads) {
+        const int T = tiles(f);
+        if (!T) continue;
+        const int per = split && T > 1 ? T : 1;
+        const int at = atomicAdd(&start[T], per);
+        if (per == 1) {
+            items[at] = f * 32 + kWhole;
+        } else {
+            for (int c = 0; c < T; ++c) items[at + c] = f * 32 + c;
+        }
+    }
 }
 
-cudaError_t launch_batched_order(const int64_t* offsets, int F, int32_t* order, cudaStream_t s) {
-    k_batched_order<<<1, kOrderThreads, 0, s>>>(offsets, F, order);
+cudaError_t launch_batched_plan(const float* lw, const int64_t* offsets, int F, const int32_t* mask, int split,
+                                int32_t* items, uint32_t* ctl, cudaStream_t s) {
+    k_batched_plan<<<1, kPlanThreads, 0, s>>>(lw, offsets, F, mask, split, items, ctl);
     return cudaGetLastError();
+}
+
+template <int KIND>
+static cudaError_t launch_batched_kind(const BatchParams& bp, int grid, cudaStream_t s) {
+    // cooperative: every CTA resident, so a CTA waiting for the other tiles of
+    // a split filter never waits on a CTA that cannot run
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = batched_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batched<KIND>, bp);
 }
 
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s) {
-    const size_t smem = batched_smem_bytes();
     switch (kind) {
-    case KIND_MULTI: k_batched<KIND_MULTI><<<grid, kThreads, smem, s>>>(bp); break;
-    case KIND_STRAT: k_batched<KIND_STRAT><<<grid, kThreads, smem, s>>>(bp); break;
-    case KIND_SYS: k_batched<KIND_SYS><<<grid, kThreads, smem, s>>>(bp); break;
+    case KIND_MULTI: return launch_batched_kind<KIND_MULTI>(bp, grid, s);
+    case KIND_STRAT: return launch_batched_kind<KIND_STRAT>(bp, grid, s);
+    case KIND_SYS: return launch_batched_kind<KIND_SYS>(bp, grid, s);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace pf

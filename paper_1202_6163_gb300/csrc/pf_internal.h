@@ -28,6 +28,7 @@ enum : int {
     CTL_METRO_B = 6,      // Metropolis step count chosen on the device
     CTL_ARRIVE0 = 8,      // arrival counters of the single-launch kernels,
     CTL_ARRIVE1 = 9,      //   used by alternate epochs (one is reset while the other counts)
+    CTL_ITEMS = 10,       // work items of the current batched call (written by its plan pass)
     CTL_WORDS = 16
 };
 
@@ -74,14 +75,11 @@ struct BatchParams {
     uint32_t* ctl;
     float* scratch;           // multinomial: per-CTA cumulative weights of multi-tile filters
     int64_t scratch_per_cta;  // floats per CTA
-    const int32_t* mask;      // optional: filters with mask[f] == 0 are skipped
-    const int32_t* order;     // optional: ticket t resamples filter order[t] (largest first)
+    const int32_t* items;     // work items from the plan pass: f * 32 + tile, or f * 32 + 31 (whole filter)
+    uint4* records;           // one 16-byte tile record per item (split filters)
+    uint32_t* counters;       // two per filter (arrivals, departures), zero between launches
+    uint64_t wait_ns;         // limit of the wait for a split filter's records
 };
-
-// Filters of a batched call ordered by decreasing size, so that the largest
-// are taken first and the persistent grid does not end on one long filter.
-constexpr int kOrderMinF = 64;        // fewer filters: natural order
-constexpr int kOrderMaxF = 1 << 20;   // more filters: natural order (one-CTA ordering pass)
 
 // One step of F bootstrap filters on the linear-Gaussian test model.
 struct LgParams {
@@ -119,7 +117,9 @@ cudaError_t launch_lg_init(const LgParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_lg_step(const LgParams& p, cudaStream_t s);
 int persistent_blocks_per_sm(int kind);
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s);
-cudaError_t launch_batched_order(const int64_t* offsets, int F, int32_t* order, cudaStream_t s);
+cudaError_t launch_batched_plan(const float* lw, const int64_t* offsets, int F, const int32_t* mask, int split,
+                                int32_t* items, uint32_t* ctl, cudaStream_t s);
+constexpr int kMaxItemsPerFilter = 16;  // tiles of a batched filter (kMaxOwnB)
 int batched_blocks_per_sm(int kind);
 size_t batched_scratch_floats_per_cta();
 cudaError_t launch_batched_metropolis(const BatchParams& bp, int grid, cudaStream_t s);

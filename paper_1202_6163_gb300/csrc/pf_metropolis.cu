@@ -123,14 +123,14 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
     extern __shared__ float wsm[];
     __shared__ int f_sm;
     const int tid = threadIdx.x;
+    const int n_items = (int)ld_relaxed_u32(bp.ctl + CTL_ITEMS);
     for (;;) {
         if (tid == 0) f_sm = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
         __syncthreads();
         const int ticket = f_sm;
         __syncthreads();
-        if (ticket >= bp.F) break;
-        const int f = bp.order ? bp.order[ticket] : ticket;
-        if (bp.mask && bp.mask[f] == 0) continue;
+        if (ticket >= n_items) break;
+        const int f = bp.items[ticket] >> 5;
         const int64_t off0 = bp.offsets[f], off1 = bp.offsets[f + 1];
         const int64_t Pf = off1 - off0;
         if (Pf <= 0 || Pf > 0x7fffffffLL) {
