@@ -279,10 +279,11 @@ pf_status pf_set_wait_limit_ns(uint64_t ns);
 
 /*
  * Fault injection for tests of the timeout path (host-side switch, read at
- * launch): when tile >= 0, the next single-launch systematic/stratified call
- * has that tile skip publishing its partial sum, so every wait on it runs out
- * and the call records PF_ERR_TIMEOUT.  The switch clears itself after one
- * call.  tile < 0 disarms it.
+ * launch): when tile >= 0, the next systematic/stratified call -- single
+ * launch, or batched, where tile `tile` of every filter split over several
+ * CTAs is meant -- has that tile skip publishing its record, so every wait on
+ * it runs out and the call records PF_ERR_TIMEOUT.  The switch clears itself
+ * after one call.  tile < 0 disarms it.
  */
 pf_status pf_debug_skip_publish(int64_t tile);
 

@@ -66,7 +66,7 @@ pf_status pf_lg_init(int F, int64_t P, int D, float m0, float p0, uint64_t seed,
  *   loglik[f]   += L - (R ? log P : log_sum[f]);   log_sum[f] = L
  *   ess[f]       = (sum_j w_j)^2 / sum_j w_j^2;      resample[f] = ess[f] < threshold * P
  * The ancestor gather is fused into the state read.  Arithmetic is FP32 per
- * particle; each block of 2048 particles reduces to (max, sum, sum of squares)
+ * particle; each block of 1024 particles reduces to (max, sum, sum of squares)
  * relative to its max, and the last block of a filter combines them and
  * updates the FP64 scalars.
  *   a        [F] float              y [F][D] float, 16-byte aligned (y_t)

@@ -366,6 +366,8 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     bp.records = reinterpret_cast<uint4*>((char*)w->scratch + records_at);
     bp.counters = w->counters;
     bp.wait_ns = g_wait_ns;
+    bp.skip_tile = kind == PF_STRATIFIED || kind == PF_SYSTEMATIC ? (int)g_skip_tile : -1;
+    if (bp.skip_tile >= 0) g_skip_tile = -1;
     if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
     return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
 }

@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
             uint32_t* arrive = bp.counters + 2 * f;
             if (tid == 0) {
                 int ok = 1;
-                if (Tf > 1) {
+                if (Tf > 1 && c == bp.skip_tile) {
+                    ok = 0;  // test hook: withhold this tile's record; the filter's other tiles time out
+                } else if (Tf > 1) {
                     st_v4_u32(rec + 4 * c, (uint32_t)ts.k, __float_as_uint(ts.S.hi), __float_as_uint(ts.S.lo),
                               (uint32_t)(ts.i_last + 1) | (ts.bad ? 0x80000000u : 0u));
                     __threadfence();

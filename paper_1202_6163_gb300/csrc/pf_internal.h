@@ -79,6 +79,7 @@ struct BatchParams {
     uint4* records;           // one 16-byte tile record per item (split filters)
     uint32_t* counters;       // two per filter (arrivals, departures), zero between launches
     uint64_t wait_ns;         // limit of the wait for a split filter's records
+    int skip_tile;            // test hook: tile skip_tile of every split filter withholds its record (-1: off)
 };
 
 // One step of F bootstrap filters on the linear-Gaussian test model.

@@ -9,7 +9,7 @@
 // and, per filter, the log-sum-exp of the new weights, the effective sample
 // size, the increment of the marginal log-likelihood and the decision to
 // resample before the next step.  The per-filter reduction is fused into the
-// producing kernel: each CTA reduces its tile of 2048 log-weights to
+// producing kernel: each CTA reduces its tile of 1024 log-weights to
 // (max, sum exp, sum exp^2) relative to its own max, and the last CTA of a
 // filter to arrive (a per-filter counter) combines the tile records.
 //
@@ -29,7 +29,7 @@
 namespace pf {
 namespace {
 
-constexpr int kLgThreads = 512;
+constexpr int kLgThreads = 256;
 constexpr int kLgPerThread = 4;
 constexpr int kLgWarps = kLgThreads / 32;
 constexpr uint32_t kTagPropagate = 6;

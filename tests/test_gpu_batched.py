@@ -106,3 +106,32 @@ def test_batched_repeatable():
     a1, _ = run_batched(pf.PF_STRATIFIED, lw, off, seeds)
     a2, _ = run_batched(pf.PF_STRATIFIED, lw, off, seeds)
     assert np.array_equal(a1, a2)
+
+
+def test_split_filter_timeout_is_reported_and_recovered():
+    # filters of several tiles are split over CTAs that wait for each other's
+    # records; a withheld record makes the waits run out (bounded), the call
+    # reports PF_ERR_TIMEOUT, and the next call is correct again
+    sizes = np.array([30000, 100, 70000, 9000], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    lw = workloads.gaussian_logw(int(off[-1]), 1.0, seed=4)
+    seeds = workloads.batched_seeds(sizes.size, base=3)
+    d_lw, d_off = torch.from_numpy(lw).cuda(), torch.from_numpy(off).cuda()
+    d_seeds = torch.from_numpy(seeds.view(np.int64)).cuda()
+    anc = torch.empty(lw.size, dtype=torch.int32, device="cuda")
+    pf.pf_set_wait_limit_ns(5_000_000)
+    try:
+        pf.pf_debug_skip_publish(1)
+        pf.pf_resample_batched(pf.PF_SYSTEMATIC, d_lw, d_off, sizes.size, 0, d_seeds, anc)
+        assert pf.pf_get_device_status() == pf.PF_ERR_TIMEOUT
+    finally:
+        pf.pf_debug_skip_publish(-1)
+        pf.pf_set_wait_limit_ns(1_000_000_000)
+    pf.pf_resample_batched(pf.PF_SYSTEMATIC, d_lw, d_off, sizes.size, 0, d_seeds, anc)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    a = anc.cpu().numpy()
+    for f in range(sizes.size):
+        l = lw[off[f]:off[f + 1]]
+        rep = check_cumulative("systematic", l, a[off[f]:off[f + 1]], oracle.systematic(l, int(seeds[f]), f),
+                               int(seeds[f]), filter_id=f)
+        assert rep.ok, (f, rep.summary())
