@@ -500,7 +500,7 @@ pf_status pf_probe_l2_random_reads(const float* buf, int64_t n, int reads_per_th
 namespace {
 bool lg_shape_ok(int F, int64_t P, int D) {
     return F >= 1 && F <= (1 << 24) && P >= 1 && P <= 0x7fffffffLL && D >= 4 && D <= 64 && D % 4 == 0 &&
-           (int64_t)F * P <= ((int64_t)1 << 40) && (P + 2047) / 2048 * (int64_t)F < 0x7fffffffLL;
+           (int64_t)F * P <= ((int64_t)1 << 40) && (P + lg_tile() - 1) / lg_tile() * (int64_t)F < 0x7fffffffLL;
 }
 }  // namespace
 
