@@ -160,6 +160,16 @@ pf_status pf_gather(const void* src, int64_t P_src, int64_t row_bytes, const int
                     int64_t P_dst, void* dst, void* stream);
 
 /*
+ * 1 if `ptr` can be passed as a device pointer to the calls above at the same
+ * address: device memory, managed memory, or page-locked host memory mapped
+ * into the device's address space (as cudaHostAlloc gives under unified
+ * addressing); 0 otherwise.  With host memory the kernels read and write it
+ * over the CPU-GPU link (NVLink-C2C on GB300), e.g. a gather whose states
+ * live in host memory.  Host-only.
+ */
+int pf_is_device_accessible(const void* ptr);
+
+/*
  * Effective sample size (Section 3 quotes ESS/P for its weight sets; the
  * standard form is used): ess_out[0] = (sum w)^2 / sum w^2, and, if
  * log_sum_out is not NULL, log_sum_out[0] = log sum_i exp(lw_i).

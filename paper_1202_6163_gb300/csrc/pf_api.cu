@@ -677,6 +677,17 @@ pf_status pf_autotune(int kind, const float* logw, int64_t P, int32_t* ancestors
     return PF_OK;
 }
 
+int pf_is_device_accessible(const void* ptr) {
+    if (!ptr) return 0;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();  // clear the error an unknown pointer leaves
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 1;
+    return a.type == cudaMemoryTypeHost && a.devicePointer == ptr ? 1 : 0;
+}
+
 int pf_version(void) { return 100; }
 
 }  // extern "C"

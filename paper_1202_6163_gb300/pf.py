@@ -34,6 +34,7 @@ SIGNATURES = {
     "pf_get_device_status": (_INT, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "pf_metropolis_B": (_I64, [_I64, ctypes.c_double, ctypes.c_double]),
     "pf_status_string": (ctypes.c_char_p, [_INT]),
+    "pf_is_device_accessible": (_INT, [_VP]),
     "pf_metropolis_bias": (ctypes.c_double, [_I64, ctypes.c_double, _I64]),
     "pf_set_wait_limit_ns": (_INT, [_U64]),
     "pf_debug_skip_publish": (_INT, [_I64]),
@@ -182,6 +183,10 @@ def pf_metropolis_B(P, w_max, eps=0.01) -> int:
 
 def pf_metropolis_bias(P, w_max, B) -> float:
     return load().pf_metropolis_bias(P, w_max, B)
+
+
+def pf_is_device_accessible(ptr) -> bool:
+    return bool(load().pf_is_device_accessible(_ptr(ptr)))
 
 
 def pf_status_string(status: int) -> str:

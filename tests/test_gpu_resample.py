@@ -372,3 +372,22 @@ def test_unaligned_inputs(kind, off):
         assert np.all(out[:o] == -5) and np.all(out[o + P:] == -5)
         rep = check_cumulative(kind, lw, a, orc(lw, 3), 3)
         assert rep.ok, rep.summary()
+
+
+def test_gather_with_host_resident_states():
+    # page-locked host memory is device-accessible at the same address: the
+    # gather reads the source rows and writes the result over the CPU-GPU link
+    P, D = 70001, 16
+    st = torch.from_numpy(workloads.states(P, D, seed=8)).pin_memory()
+    out = torch.full((P, D), -1.0).pin_memory()
+    assert pf.pf_is_device_accessible(st.data_ptr()) and pf.pf_is_device_accessible(out.data_ptr())
+    assert pf.pf_is_device_accessible(torch.zeros(4, device="cuda").data_ptr())
+    assert not pf.pf_is_device_accessible(np.zeros(1024, np.float32).ctypes.data)
+    assert not pf.pf_is_device_accessible(None)
+    lw = workloads.gaussian_logw(P, 1.0, seed=9)
+    a, st_code = gpu_resample(pf.pf_resample_systematic, lw, 5)
+    assert st_code == pf.PF_OK
+    pf.pf_gather(st.data_ptr(), P, 4 * D, torch.from_numpy(a).cuda(), P, out.data_ptr())
+    torch.cuda.synchronize()
+    assert pf.pf_get_device_status() == pf.PF_OK
+    np.testing.assert_array_equal(out.numpy(), st.numpy()[a])
