@@ -160,6 +160,33 @@ pf_status pf_gather(const void* src, int64_t P_src, int64_t row_bytes, const int
                     int64_t P_dst, void* dst, void* stream);
 
 /*
+ * Ancestors in the form for in-place moves (Section 2: offspring and
+ * ancestors are interchangeable).  From any ancestor vector a (offspring
+ * counts o_i = #{j : a_j = i}), writes the vector with the same counts in
+ * which every particle with offspring keeps one of them in its own slot
+ * (permuted[i] = i) and the other o_i - 1 copies of each such i, in
+ * increasing i, fill the slots of the particles without offspring, in
+ * increasing slot order.  Then permuted[permuted[j]] = permuted[j], and
+ * pf_gather_inplace moves the states without a second buffer.  Deterministic.
+ *   ancestors [P] int32 (in), permuted [P] int32 (out), 4-byte aligned, not
+ *   overlapping.  Uses 3P + P/1024 ints of workspace.
+ * Errors: PF_ERR_INVALID for bad arguments (returned) or an ancestor outside
+ * [0, P) (device status; the output is then unspecified).
+ */
+pf_status pf_permute(const int32_t* ancestors, int64_t P, int32_t* permuted, void* stream);
+
+/*
+ * In-place ancestor gather: row j of x <- row permuted[j] wherever they
+ * differ, for a vector in the form pf_permute gives (a source row keeps its
+ * slot, so no row is read after it is written).  Only the rows of particles
+ * without offspring are written.
+ *   x [P][row_bytes] (in/out), row_bytes a positive multiple of 4
+ * A permuted[j] outside [0, P) or whose own entry is not itself leaves row j
+ * untouched and sets device status PF_ERR_INVALID.
+ */
+pf_status pf_gather_inplace(void* x, int64_t P, int64_t row_bytes, const int32_t* permuted, void* stream);
+
+/*
  * 1 if `ptr` can be passed as a device pointer to the calls above at the same
  * address: device memory, managed memory, or page-locked host memory mapped
  * into the device's address space (as cudaHostAlloc gives under unified

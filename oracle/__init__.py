@@ -86,6 +86,7 @@ def _load():
             "orc_metropolis_B": (i64, [i64, ctypes.c_double, ctypes.c_double]),
             "orc_batched": (i32, [i32, c_f, c_i64, i32, i32, c_u64, c_i32]),
             "orc_kalman_loglik": (ctypes.c_double, [ctypes.c_double] * 5 + [c_d, i32, i32]),
+            "orc_permute": (i32, [c_i32, i64, c_i32]),
             "orc_lg_normals": (None, [u64, u32, u32, u32, c_d]),
             "orc_lg_init": (i32, [i32, i64, i32, ctypes.c_double, ctypes.c_double, u64, c_d, c_d, c_d, c_d, c_d,
                                   c_i32]),
@@ -373,3 +374,15 @@ def lg_filter(a, q, r, y, seed, step_seeds, P, m0=0.0, p0=1.0, threshold=0.5, ki
                                  float(p0), float(threshold), _p(y, ctypes.c_float), T, seed,
                                  _p(ss, ctypes.c_uint64), _p(ll, ctypes.c_double)))
     return ll
+
+
+# --------------------------------------------------------------------------
+# Offspring/ancestor conversion for in-place moves (Section 2).
+# --------------------------------------------------------------------------
+def permute(anc):
+    """Ancestors with the same offspring counts, every particle with offspring
+    keeping one in its own slot, the other copies filling the empty slots in order."""
+    anc = np.ascontiguousarray(anc, dtype=np.int32)
+    out = np.zeros(anc.size, dtype=np.int32)
+    _check(_load().orc_permute(_p(anc, ctypes.c_int32), anc.size, _p(out, ctypes.c_int32)))
+    return out

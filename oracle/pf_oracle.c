@@ -704,3 +704,40 @@ int orc_lg_filter(int kind, int F, int64_t P, int D, const float* a, double q, d
     free(x); free(xn); free(lw); free(c); free(u); free(anc); free(log_sum); free(ess); free(resample);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Offspring/ancestor conversion (Section 2: the stratified and systematic  */
+/* schemes yield offspring counts, the others ancestors; converting is      */
+/* direct) in the form that lets particles be moved in place: every        */
+/* particle i with offspring keeps one of them in its own slot (out[i] = i), */
+/* and the other offspring (o_i - 1 copies of each i, in increasing i) fill  */
+/* the slots of the particles without offspring, in increasing slot order.   */
+/* out has the same offspring counts as anc, and out[out[j]] = out[j].       */
+/* ------------------------------------------------------------------------ */
+int orc_permute(const int32_t* anc, int64_t P, int32_t* out)
+{
+    if (P < 1) return ORC_ERR_INVALID;
+    int64_t* o = (int64_t*)calloc((size_t)P, sizeof(int64_t));
+    if (!o) return ORC_ERR_INVALID;
+    for (int64_t j = 0; j < P; ++j) {
+        if (anc[j] < 0 || anc[j] >= P) { free(o); return ORC_ERR_INVALID; }
+        o[anc[j]] += 1;
+    }
+    int64_t next_extra = 0, left = 0; /* the particle whose extra copies are being placed, and how many remain */
+    while (next_extra < P && o[next_extra] <= 1) ++next_extra;
+    if (next_extra < P) left = o[next_extra] - 1;
+    for (int64_t i = 0; i < P; ++i) {
+        if (o[i] > 0) {
+            out[i] = (int32_t)i;
+        } else {
+            out[i] = (int32_t)next_extra;
+            if (--left == 0) {
+                ++next_extra;
+                while (next_extra < P && o[next_extra] <= 1) ++next_extra;
+                if (next_extra < P) left = o[next_extra] - 1;
+            }
+        }
+    }
+    free(o);
+    return ORC_OK;
+}

@@ -677,6 +677,38 @@ pf_status pf_autotune(int kind, const float* logw, int64_t P, int32_t* ancestors
     return PF_OK;
 }
 
+pf_status pf_permute(const int32_t* ancestors, int64_t P, int32_t* permuted, void* stream) {
+    if (!ancestors || !permuted || P < 1 || P > PF_MAX_PARTICLES) return PF_ERR_INVALID;
+    if (((uintptr_t)ancestors & 3u) || ((uintptr_t)permuted & 3u)) return PF_ERR_INVALID;
+    const uintptr_t a0 = (uintptr_t)ancestors, p0 = (uintptr_t)permuted, n = (uintptr_t)P * 4;
+    if (a0 < p0 + n && p0 < a0 + n) return PF_ERR_INVALID;  // must not overlap
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    Workspace* w;
+    st = workspace(s, permute_scratch_bytes(P), w);
+    if (st) return st;
+    return cuda_fail(launch_permute(ancestors, P, permuted, w->scratch, w->ctl, info->num_sms, s), "permute launch");
+}
+
+pf_status pf_gather_inplace(void* x, int64_t P, int64_t row_bytes, const int32_t* permuted, void* stream) {
+    if (!x || !permuted || P < 1 || P > PF_MAX_PARTICLES || row_bytes < 4 || (row_bytes & 3)) return PF_ERR_INVALID;
+    if (((uintptr_t)x & 3u) || ((uintptr_t)permuted & 3u)) return PF_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    DeviceInfo* info;
+    pf_status st = device_info(dev, info);
+    if (st) return st;
+    Workspace* w;
+    st = workspace(s, 0, w);
+    if (st) return st;
+    return cuda_fail(launch_gather_inplace(x, P, row_bytes, permuted, w->ctl, info->num_sms, s), "gather launch");
+}
+
 int pf_is_device_accessible(const void* ptr) {
     if (!ptr) return 0;
     cudaPointerAttributes a;

@@ -116,6 +116,11 @@ cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, 
 int lg_tile();
 cudaError_t launch_lg_init(const LgParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_lg_step(const LgParams& p, cudaStream_t s);
+size_t permute_scratch_bytes(int64_t P);
+cudaError_t launch_permute(const int32_t* anc, int64_t P, int32_t* out, void* scratch, uint32_t* ctl, int num_sms,
+                           cudaStream_t s);
+cudaError_t launch_gather_inplace(void* x, int64_t P, int64_t row_bytes, const int32_t* perm, uint32_t* ctl,
+                                  int num_sms, cudaStream_t s);
 int persistent_blocks_per_sm(int kind);
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s);
 cudaError_t launch_batched_plan(const float* lw, const int64_t* offsets, int F, const int32_t* mask, int split,

@@ -35,6 +35,8 @@ SIGNATURES = {
     "pf_metropolis_B": (_I64, [_I64, ctypes.c_double, ctypes.c_double]),
     "pf_status_string": (ctypes.c_char_p, [_INT]),
     "pf_is_device_accessible": (_INT, [_VP]),
+    "pf_permute": (_INT, [_VP, _I64, _VP, _VP]),
+    "pf_gather_inplace": (_INT, [_VP, _I64, _I64, _VP, _VP]),
     "pf_metropolis_bias": (ctypes.c_double, [_I64, ctypes.c_double, _I64]),
     "pf_set_wait_limit_ns": (_INT, [_U64]),
     "pf_debug_skip_publish": (_INT, [_I64]),
@@ -183,6 +185,14 @@ def pf_metropolis_B(P, w_max, eps=0.01) -> int:
 
 def pf_metropolis_bias(P, w_max, B) -> float:
     return load().pf_metropolis_bias(P, w_max, B)
+
+
+def pf_permute(ancestors, P, permuted, stream=None):
+    _check(load().pf_permute(_ptr(ancestors), P, _ptr(permuted), _stream(stream)), "pf_permute")
+
+
+def pf_gather_inplace(x, P, row_bytes, permuted, stream=None):
+    _check(load().pf_gather_inplace(_ptr(x), P, row_bytes, _ptr(permuted), _stream(stream)), "pf_gather_inplace")
 
 
 def pf_is_device_accessible(ptr) -> bool:

@@ -391,3 +391,48 @@ def test_gather_with_host_resident_states():
     torch.cuda.synchronize()
     assert pf.pf_get_device_status() == pf.PF_OK
     np.testing.assert_array_equal(out.numpy(), st.numpy()[a])
+
+
+@pytest.mark.parametrize("P", [1, 7, 4096, 4097, 100003, 1 << 20])
+def test_permute_matches_oracle_and_inplace_gather(P):
+    rng = np.random.default_rng(P)
+    cases = [rng.integers(0, P, size=P).astype(np.int32),
+             np.sort(rng.integers(0, P, size=P)).astype(np.int32),
+             np.full(P, P // 2, np.int32), np.arange(P, dtype=np.int32)]
+    lw = workloads.gaussian_logw(P, 2.0, seed=P)
+    a, st = gpu_resample(pf.pf_resample_systematic, lw, 3)
+    assert st == pf.PF_OK
+    cases.append(a)
+    for anc in cases:
+        d_anc = torch.from_numpy(anc).cuda()
+        perm = torch.full((P,), -9, dtype=torch.int32, device="cuda")
+        pf.pf_permute(d_anc, P, perm)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        np.testing.assert_array_equal(perm.cpu().numpy(), oracle.permute(anc))
+    # in-place move of the states equals the out-of-place gather by the permuted ancestors
+    D = 8
+    x = torch.from_numpy(workloads.states(P, D, seed=1)).cuda()
+    ref = x[perm.long()].clone()
+    pf.pf_gather_inplace(x, P, 4 * D, perm)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    assert torch.equal(x, ref)
+
+
+def test_permute_and_inplace_gather_errors():
+    P = 1000
+    bad = torch.arange(P, dtype=torch.int32, device="cuda")
+    bad[5] = P
+    out = torch.empty(P, dtype=torch.int32, device="cuda")
+    pf.pf_permute(bad, P, out)
+    assert pf.pf_get_device_status() == pf.PF_ERR_INVALID
+    with pytest.raises(pf.PFError):
+        pf.pf_permute(bad, P, bad)  # overlapping
+    # a vector not in the in-place form: entry 3 reads row 4, which is itself overwritten
+    perm = torch.arange(P, dtype=torch.int32, device="cuda")
+    perm[3], perm[4] = 4, 5
+    x = torch.arange(P * 4, dtype=torch.float32, device="cuda").view(P, 4)
+    x0 = x.clone()
+    pf.pf_gather_inplace(x, P, 16, perm)
+    assert pf.pf_get_device_status() == pf.PF_ERR_INVALID
+    assert torch.equal(x[3], x0[3])  # left untouched
+    assert torch.equal(x[4], x0[5])
