@@ -156,7 +156,8 @@ def run_gpu(args):
         leg = {"batched": lambda: run_batched_compare(args, pf, torch, dev, stream, hbm_peak),
                "bootstrap": lambda: run_bootstrap(args, pf, torch, dev, hbm_peak),
                "figure2": lambda: run_figure2(args, pf, torch, dev),
-               "metropolis": lambda: run_metropolis_sweep(args, pf, torch, dev)}[args.only]()
+               "metropolis": lambda: run_metropolis_sweep(args, pf, torch, dev),
+               "inplace": lambda: run_inplace(args, pf, torch, dev)}[args.only]()
         if rank == 0:
             print(json.dumps({"leg": args.only, **leg}))
         return
@@ -688,6 +689,52 @@ def run_metropolis_sweep(args, pf, torch, dev):
             "rows": rows}
 
 
+def run_inplace(args, pf, torch, dev):
+    """Out-of-place gather against the in-place form (pf_permute, then
+    pf_gather_inplace) at P = 2^20, states P x 16 float32, systematic ancestors
+    of N(0, s^2) log-weights (L2 flushed before each timed call)."""
+    from paper_1202_6163_gb300 import workloads
+    s = torch.cuda.current_stream(dev)
+    stream = s.cuda_stream
+    P, D = 1 << 20, 16
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    src = torch.from_numpy(workloads.states(P, D, seed=3)).to(dev)
+    dst = torch.empty_like(src)
+    anc = torch.empty(P, dtype=torch.int32, device=dev)
+    perm = torch.empty_like(anc)
+    pf.pf_reserve(P, 0, 0, stream)
+    rows = []
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            z.record(s)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(z) * 1e3)
+        return statistics.median(ts)
+
+    for sp in (1.0, 2.0):
+        lw = torch.from_numpy(workloads.gaussian_logw(P, sp, seed=7)).to(dev)
+        pf.pf_resample_systematic(lw, P, 0, 1, anc, stream)
+        survivors = int(torch.unique(anc).numel())
+        t_gather = timed(lambda: pf.pf_gather(src, P, 4 * D, anc, P, dst, stream))
+        t_perm = timed(lambda: pf.pf_permute(anc, P, perm, stream))
+        pf.pf_permute(anc, P, perm, stream)
+        t_inplace = timed(lambda: pf.pf_gather_inplace(src, P, 4 * D, perm, stream))
+        rows.append({"s": sp, "distinct_ancestors": survivors, "gather_us": round(t_gather, 2),
+                     "permute_us": round(t_perm, 2), "gather_inplace_us": round(t_inplace, 2),
+                     "rows_moved_in_place": P - survivors})
+    if pf.pf_get_device_status(s) != pf.PF_OK:
+        raise RuntimeError("device status not OK in the in-place leg")
+    return {"workload": "P=2^20, states Px16 f32, systematic ancestors of N(0,s^2) log-weights", "rows": rows}
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_step_time(P, metro_chains, seed):
     """One step of the oracle over a bounded sample: the three cumulative resamplers, ESS
@@ -781,7 +828,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-bootstrap", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis"], default=None,
+    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace"], default=None,
                     help="run one secondary leg alone and print its JSON (for profiling)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
