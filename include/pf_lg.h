@@ -29,7 +29,9 @@
  * for particle j, dimension group g (t = 0 for the initial draw); the four
  * words give N(0,1) draws for dimensions 4g..4g+3 by the Box-Muller
  * transform: words (0,1) -> sqrt(-2 ln u(w0)) (cos, sin)(2 pi u(w1)), words
- * (2,3) likewise, with u = u23 of pf.h.
+ * (2,3) likewise, with u = u23 of pf.h.  The device evaluates the sine and
+ * cosine in hardware on the angle reduced to (-pi, pi): each draw is within
+ * about 6e-7 sqrt(-2 ln u(w0)) of the exact value.
  *
  * This model is test infrastructure for the resampling library (the paper
  * gives the filter, not this model); the library's resampling calls do not
