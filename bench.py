@@ -157,7 +157,8 @@ def run_gpu(args):
                "bootstrap": lambda: run_bootstrap(args, pf, torch, dev, hbm_peak),
                "figure2": lambda: run_figure2(args, pf, torch, dev),
                "metropolis": lambda: run_metropolis_sweep(args, pf, torch, dev),
-               "inplace": lambda: run_inplace(args, pf, torch, dev)}[args.only]()
+               "inplace": lambda: run_inplace(args, pf, torch, dev),
+               "sweep": lambda: run_size_sweep(args, pf, torch, dev, hbm_peak)}[args.only]()
         if rank == 0:
             print(json.dumps({"leg": args.only, **leg}))
         return
@@ -735,6 +736,64 @@ def run_inplace(args, pf, torch, dev):
     return {"workload": "P=2^20, states Px16 f32, systematic ancestors of N(0,s^2) log-weights", "rows": rows}
 
 
+def run_size_sweep(args, pf, torch, dev, hbm_peak):
+    """Every single-filter call over P = 2^10 ... 2^24 (N(0,1) log-weights,
+    states P x 16 for the gather): median time of 20 calls with L2 flushed
+    before each, ancestors/s, and the fraction of the measured HBM copy rate
+    (of the measured random-L2-read rate for Metropolis, B = 32; past 2^22
+    the log-weights no longer fit in L2 and the chains read HBM)."""
+    from paper_1202_6163_gb300 import workloads
+    s = torch.cuda.current_stream(dev)
+    stream = s.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    Pmax = 1 << 24
+    pf.pf_reserve(Pmax, 0, 0, stream)
+    lw_all = torch.from_numpy(workloads.gaussian_logw(Pmax, 1.0, seed=5)).to(dev)
+    anc = torch.empty(Pmax, dtype=torch.int32, device=dev)
+    st = torch.empty((Pmax, 16), device=dev)
+    dst = torch.empty_like(st)
+    ess = torch.zeros(1, device=dev)
+    l2_rate = pf.pf_probe_l2_random_reads(lw_all, 1 << 20, 256)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            z.record(s)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(z) * 1e3)
+        return statistics.median(ts)
+
+    rows = []
+    for k in range(10, 25, 2):
+        P = 1 << k
+        lw = lw_all[:P]
+        row = {"P": P}
+        for name, fn in (("systematic", pf.pf_resample_systematic), ("stratified", pf.pf_resample_stratified),
+                         ("multinomial", pf.pf_resample_multinomial)):
+            us = timed(lambda: fn(lw, P, 0, 1, anc, stream))
+            row[name] = {"us": round(us, 2), "ancestors_per_s": round(P / (us * 1e-6), 1),
+                         "hbm_frac": round(8 * P / (us * 1e-6) / 1e9 / hbm_peak, 4)}
+        us = timed(lambda: pf.pf_resample_metropolis(lw, P, METRO_B, 1, anc, stream))
+        row["metropolis_B32"] = {"us": round(us, 2), "ancestors_per_s": round(P / (us * 1e-6), 1),
+                                 "l2_frac": round(P * METRO_B / (us * 1e-6) / l2_rate, 4)}
+        us = timed(lambda: pf.pf_ess(lw, P, ess, None, stream))
+        row["ess"] = {"us": round(us, 2), "hbm_frac": round(4 * P / (us * 1e-6) / 1e9 / hbm_peak, 4)}
+        pf.pf_resample_systematic(lw, P, 0, 1, anc, stream)
+        us = timed(lambda: pf.pf_gather(st, P, 64, anc, P, dst, stream))
+        row["gather_16f"] = {"us": round(us, 2), "hbm_frac": round(132 * P / (us * 1e-6) / 1e9 / hbm_peak, 4)}
+        rows.append(row)
+    if pf.pf_get_device_status(s) != pf.PF_OK:
+        raise RuntimeError("device status not OK in the size sweep")
+    return {"workload": "single filter, P = 2^10..2^24, log-weights N(0,1) f32, states Px16 f32",
+            "l2_random_reads_per_s": round(l2_rate, 1), "hbm_peak_gbs": hbm_peak, "rows": rows}
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_step_time(P, metro_chains, seed):
     """One step of the oracle over a bounded sample: the three cumulative resamplers, ESS
@@ -828,7 +887,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-bootstrap", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace"], default=None,
+    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace", "sweep"],
+                    default=None,
                     help="run one secondary leg alone and print its JSON (for profiling)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
