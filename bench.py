@@ -52,10 +52,8 @@ def load_peaks():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1202_6163_gb300.replicas import dist_env as _d
+    return _d()
 
 
 class ClockSampler:
@@ -248,14 +246,11 @@ def run_gpu(args):
     status = pf.pf_get_device_status(stream)
     if status != pf.PF_OK:
         raise RuntimeError(f"device status {status} after the timed steps")
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-
-    ms_per_step = total_ms / args.steps
+    from paper_1202_6163_gb300.replicas import job_rate, max_over_ranks
     ancestors_per_step = 4 * P
-    value = world * ancestors_per_step * args.steps / (total_ms / 1e3)
+    value = job_rate(ancestors_per_step * args.steps, total_ms / 1e3, dev)  # all ranks' units / slowest rank
+    total_ms = max_over_ranks(total_ms, dev)
+    ms_per_step = total_ms / args.steps
 
     hbm_peak, peak_kind = load_peaks()
     # algorithmic bytes per launch

@@ -436,3 +436,43 @@ def test_permute_and_inplace_gather_errors():
     assert pf.pf_get_device_status() == pf.PF_ERR_INVALID
     assert torch.equal(x[3], x0[3])  # left untouched
     assert torch.equal(x[4], x0[5])
+
+
+def test_single_filter_calls_in_a_cuda_graph():
+    # the single-launch kernels keep their barrier counters on the device
+    # (alternating epochs), so a captured step replays without host resets
+    P, D = 300007, 16
+    lw = to_dev(workloads.gaussian_logw(P, 1.0, seed=12))
+    src = torch.from_numpy(workloads.states(P, D, seed=13)).cuda()
+    s = torch.cuda.Stream()
+    pf.pf_reserve(P, 0, 0, s)
+    anc = [torch.empty(P, dtype=torch.int32, device="cuda") for _ in range(4)]
+    dst = torch.empty_like(src)
+    ess = torch.zeros(1, device="cuda")
+
+    def step():
+        pf.pf_ess(lw, P, ess, None, s)
+        pf.pf_resample_systematic(lw, P, 0, 21, anc[0], s)
+        pf.pf_resample_stratified(lw, P, 0, 21, anc[1], s)
+        pf.pf_resample_multinomial(lw, P, 0, 21, anc[2], s)
+        pf.pf_resample_metropolis(lw, P, 16, 21, anc[3], s)
+        pf.pf_gather(src, P, 4 * D, anc[0], P, dst, s)
+
+    with torch.cuda.stream(s):
+        step()
+    s.synchronize()
+    assert pf.pf_get_device_status(s) == pf.PF_OK
+    eager = [a.clone() for a in anc] + [dst.clone(), ess.clone()]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        step()
+    for _ in range(3):
+        for a in anc:
+            a.fill_(-1)
+        dst.zero_()
+        with torch.cuda.stream(s):
+            g.replay()
+        s.synchronize()
+        assert pf.pf_get_device_status(s) == pf.PF_OK
+        for x, y in zip(anc + [dst, ess], eager):
+            assert torch.equal(x, y)
