@@ -33,6 +33,7 @@ constexpr int kMaxOwnB = 16;  // tiles per filter: P_f + lead <= 16 * kTileMax
 static_assert(PF_MAX_BATCHED_FILTER == (long long)kMaxOwnB * kTileMax, "batched filter capacity");
 static_assert(kMaxOwnB <= 31, "the carries give one tile to each lane of warp 0; item codes use 5 bits");
 static_assert(kMaxOwnB == kMaxItemsPerFilter, "items per filter");
+static_assert(kMaxOwnB * (kTileMax / kWin) <= kIoCap, "coarse samples of a multinomial filter fit the staging region");
 constexpr int kWhole = 31;  // item code: the whole filter in one CTA
 
 struct BatchShared {
@@ -216,7 +217,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                 sm.rsl[c] = ts.S.lo;
                 sm.ril[c] = ts.i_last;
             }
-            if (KIND == KIND_MULTI) write_tile_v(p, th, t0, n);
+            if (KIND == KIND_MULTI) {
+                write_tile_v(p, th, t0, n);
+                // several tiles: the coarse samples go to the (otherwise unused) staging region
+                if (Tf > 1) write_tile_coarse(th, n, reinterpret_cast<float*>(region) + c * (kTileMax / kWin));
+            }
             __syncthreads();
         }
         if (tid < 32) {
@@ -232,11 +237,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
             for (int64_t q = tid; q < nq; q += kThreads) {
                 const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
                 int32_t a[4];
-                if (Tf == 1)
+                if (Tf == 1) {
                     multinomial_draws4<true>(r, sm.table, Tf, p.v_out, kTileMax, PA, lead, sm.as.W_hi, sm.as.W_lo, a);
-                else
-                    multinomial_draws4<false>(r, sm.table, Tf, p.v_out, kTileMax, PA, lead, sm.as.W_hi, sm.as.W_lo,
-                                              a);
+                } else {
+                    const float* coarse = reinterpret_cast<const float*>(region);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+                        a[s] = multinomial_draw_windowed(word_of(r, s), sm.table, Tf, p.v_out, coarse, kTileMax / kWin,
+                                                         kTileMax, PA, lead, sm.as.W_hi, sm.as.W_lo);
+                }
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
                     if (4 * q + s < Pf) p.anc[4 * q + s] = a[s];
