@@ -211,7 +211,21 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
         return PF_ERR_INVALID;  // P beyond kMaxTilesTotal full tiles
     }
     Workspace* w;
-    st = workspace(s, kind == PF_MULTINOMIAL ? (size_t)PA * sizeof(float) : 0, w);
+    // multinomial: the tiles' cumulative weights (PA floats), then samples of
+    // every 16th (c2) and 256th (c1) for the three-level draws, when the c1
+    // samples fit in shared memory beside the tile table
+    int cpt2 = 0, cpt1 = 0;
+    size_t c2_at = 0, c1_at = 0, mscratch = 0;
+    if (kind == PF_MULTINOMIAL) {
+        cpt2 = ((tile + 15) / 16 + 15) & ~15;
+        cpt1 = (tile + 255) / 256;
+        if ((size_t)T * sizeof(float4) + (size_t)T * cpt1 * sizeof(float) > (size_t)kMaxTilesTotal * sizeof(float4))
+            cpt1 = cpt2 = 0;
+        c2_at = ((size_t)PA * sizeof(float) + 255) & ~(size_t)255;
+        c1_at = (c2_at + (size_t)T * cpt2 * sizeof(float) + 255) & ~(size_t)255;
+        mscratch = c1_at + (size_t)T * cpt1 * sizeof(float);
+    }
+    st = workspace(s, mscratch, w);
     if (st) return st;
     SortedParams p;
     p.lw = logw - lead;
@@ -231,6 +245,10 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     p.skip_tile = (int)g_skip_tile;
     g_skip_tile = -1;
     p.v_out = kind == PF_MULTINOMIAL ? (float*)w->scratch : nullptr;
+    p.c2_out = cpt2 > 0 ? reinterpret_cast<float*>((char*)w->scratch + c2_at) : nullptr;
+    p.c1_out = cpt2 > 0 ? reinterpret_cast<float*>((char*)w->scratch + c1_at) : nullptr;
+    p.cpt2 = cpt2;
+    p.cpt1 = cpt1;
     return cuda_fail(launch_sorted_persistent(kind, p, G, s), "persistent launch");
 }
 
@@ -392,7 +410,10 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     DeviceInfo* info;
     pf_status st = device_info(dev, info);
     if (st) return st;
-    size_t need = (size_t)P_max * sizeof(float);
+    // multinomial: P + 3 floats of cumulative weights and their 1/16 and 1/256 samples
+    size_t need = (((size_t)(P_max + 3) * sizeof(float) + 255) & ~(size_t)255) +
+                  (((size_t)(P_max + 3) / 16 + 16 * (size_t)kMaxTilesTotal) * sizeof(float) + 255) / 256 * 256 +
+                  ((size_t)(P_max + 3) / 256 + (size_t)kMaxTilesTotal) * sizeof(float);
     const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
     if (red > need) need = red;
     if (F_max > 0) {

@@ -402,6 +402,103 @@ __device__ __forceinline__ void write_tile_coarse(const TileThread& th, int n, f
     }
 }
 
+// Count of the first n (<= 16) entries of a 16-aligned window of |values|
+// at or below the tile-local target (xh, xl); the window is monotone, so the
+// count is the index of the first entry above it (n if none).
+__device__ __forceinline__ int window_below(const float* w, int n, float xh, float xl) {
+    int below = 0;
+    if (n == 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t4 = __ldcg(reinterpret_cast<const float4*>(w) + q);
+            below += (__fsub_rn(fabsf(t4.x), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.y), xh) > xl ? 0 : 1) +
+                     (__fsub_rn(fabsf(t4.z), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.w), xh) > xl ? 0 : 1);
+        }
+    } else {
+        for (int i = 0; i < n; ++i) below += __fsub_rn(fabsf(__ldcg(w + i)), xh) > xl ? 0 : 1;
+    }
+    return below;
+}
+
+// Single-launch multinomial draw over three levels of the tiles' cumulative
+// weights: every 256th |v| of each tile (c1, shared memory), every 16th (c2,
+// global, cpt2 per tile, each tile's block 64-byte aligned) and v itself
+// (global).  Each level narrows to a window of 16 entries of the next, read
+// whole; the predicate and the monotone sequence are those of the plain
+// search, so the result is the same, with two dependent 64-byte reads per
+// draw instead of a dozen dependent 4-byte reads.
+__device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const TableEntry* table, int T, const float* v,
+                                                           const float* c2, int cpt2, const float* c1, int cpt1,
+                                                           int tile, int64_t PA, int lead, float Wh, float Wl) {
+    float uh, ul;
+    u32_pair(x, uh, ul);
+    const float th = __fmul_rn(uh, Wh);
+    const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const float d = __fadd_rn(__fsub_rn(table[mid].bhi, th), __fsub_rn(table[mid].blo, tl));
+        if (d <= 0.f) lo = mid;
+        else hi = mid - 1;
+    }
+    while (lo > 0 && table[lo].il < 0) --lo;
+    const TableEntry e = table[lo];
+    float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
+    float xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
+    if (xh + xl < 0.f) {
+        xh = 0.f;
+        xl = 0.f;
+    }
+    const int64_t b0 = (int64_t)lo * tile;
+    const int nt = (int)min((int64_t)tile, PA - b0);
+    const int n2 = (nt + 15) >> 4, n1 = (nt + 255) >> 8;
+    // level 1: first 256-element window whose last sample is above the target
+    const float* c = c1 + lo * cpt1;
+    int cl = 0, cn = n1;
+    while (cn > 0) {
+        const int half = cn >> 1;
+        if (__fsub_rn(c[cl + half], xh) > xl) {
+            cn = half;
+        } else {
+            cl += half + 1;
+            cn -= half + 1;
+        }
+    }
+    int idx = e.il;
+    if (cl < n1) {
+        // level 2: the 16 samples of that window, then level 3: the 16 elements
+        const int m2 = (cl << 4) + window_below(c2 + (int64_t)lo * cpt2 + (cl << 4), min(16, n2 - (cl << 4)), xh, xl);
+        const int w0 = m2 << 4;
+        const int below = window_below(v + b0 + w0, min(16, nt - w0), xh, xl);
+        idx = w0 + below;
+        if (below >= min(16, nt - w0)) idx = e.il;  // not reached: the window's last sample is above the target
+        else if (zero_flag(__ldcg(v + b0 + idx))) {  // rounding landed on a zero weight: the next positive one
+            int f = e.il;
+            for (int z = idx + 1; z < nt; ++z)
+                if (!zero_flag(__ldcg(v + b0 + z))) {
+                    f = z;
+                    break;
+                }
+            idx = f;
+        }
+    }
+    return (int32_t)(b0 + idx - lead);
+}
+
+// This thread's samples of its tile: every 16th |v| (and the tile's last)
+// into c2, every 256th (and the last) into c1.
+__device__ __forceinline__ void write_tile_samples(const TileThread& th, int n, float* c2, float* c1) {
+#pragma unroll
+    for (int i = 0; i < kMaxPerThread; ++i) {
+        const int e = th.e0 + i;
+        if (i < th.K && e < n) {
+            const bool lastel = e == n - 1;
+            if (((e + 1) & 15) == 0 || lastel) c2[e >> 4] = fabsf(th.v[i]);
+            if (((e + 1) & 255) == 0 || lastel) c1[e >> 8] = fabsf(th.v[i]);
+        }
+    }
+}
+
 // Reloads a tile stored by write_tile_v into th (elements of tile-local
 // indices [0, n)): v from the magnitudes, the positive-weight mask from the
 // sign bits.  Slots at or beyond n are not read.

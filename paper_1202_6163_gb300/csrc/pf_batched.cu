@@ -73,6 +73,9 @@ __device__ __forceinline__ void filter_params(const BatchParams& bp, int f, int6
     p.skip_tile = -1;
     p.lead = lead;
     p.v_out = nullptr;
+    p.c2_out = nullptr;
+    p.c1_out = nullptr;
+    p.cpt2 = p.cpt1 = 0;
 }
 
 // Warp 0: the exact fixed-point carries of a filter's Tf tiles from their

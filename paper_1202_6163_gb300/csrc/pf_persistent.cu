@@ -154,10 +154,24 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
     const float Wh = sm.as.W_hi, Wl = sm.as.W_lo;
     const int64_t nq = (p.P + 3) >> 2;  // four draws per Philox block
     const int64_t q_beg = nq * cta / G, q_end = nq * (cta + 1) / G;
+    // the level-1 samples of every tile, after the table (published before the arrival)
+    float* c1 = reinterpret_cast<float*>(const_cast<TableEntry*>(table) + T);
+    if (p.c2_out) {
+        const int nc = T * p.cpt1;
+        for (int i = tid; i < nc; i += kThreads) c1[i] = __ldcg(p.c1_out + i);
+        __syncthreads();
+    }
     for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
         const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
         int32_t a[4];
-        multinomial_draws4<false>(r, table, T, p.v_out, p.tile, p.P + p.lead, p.lead, Wh, Wl, a);
+        if (p.c2_out) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                a[s] = multinomial_draw_3level(word_of(r, s), table, T, p.v_out, p.c2_out, p.cpt2, c1, p.cpt1, p.tile,
+                                               p.P + p.lead, p.lead, Wh, Wl);
+        } else {
+            multinomial_draws4<false>(r, table, T, p.v_out, p.tile, p.P + p.lead, p.lead, Wh, Wl, a);
+        }
         const int64_t j = 4 * q;
         if (j + 3 < p.P && (((uintptr_t)(p.anc + j)) & 15u) == 0) {
             *reinterpret_cast<int4*>(p.anc + j) = make_int4(a[0], a[1], a[2], a[3]);
@@ -196,6 +210,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
         if (KIND == KIND_MULTI) {
             write_tile_v(p, th, t0, n);
+            if (p.c2_out) write_tile_samples(th, n, p.c2_out + (int64_t)t * p.cpt2, p.c1_out + (int64_t)t * p.cpt1);
             __threadfence();
         }
         if (tid == 0) {
@@ -246,7 +261,8 @@ static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = persistent_smem_bytes(KIND, p.n_tiles);
+    cfg.dynamicSmemBytes =
+        persistent_smem_bytes(KIND, p.n_tiles) + (p.c2_out ? (size_t)p.n_tiles * p.cpt1 * sizeof(float) : 0);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
