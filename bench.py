@@ -216,6 +216,8 @@ def run_gpu(args):
     sampler.start()
     time.sleep(0.3)
     per_kernel = {k: 0.0 for k in kernels}
+    per_kernel_steps = {k: [] for k in kernels}
+    step_ms = []
     total_ms = 0.0
     if world > 1:
         torch.distributed.barrier()
@@ -231,15 +233,19 @@ def run_gpu(args):
         if len(ev_sets) >= 64:
             torch.cuda.synchronize(dev)
             for e in ev_sets:
-                total_ms += e[0].elapsed_time(e[6])
+                step_ms.append(e[0].elapsed_time(e[6]))
+                total_ms += step_ms[-1]
                 for i, k in enumerate(kernels):
                     per_kernel[k] += e[i].elapsed_time(e[i + 1])
+                    per_kernel_steps[k].append(e[i].elapsed_time(e[i + 1]))
             ev_sets = []
     torch.cuda.synchronize(dev)
     for e in ev_sets:
-        total_ms += e[0].elapsed_time(e[6])
+        step_ms.append(e[0].elapsed_time(e[6]))
+        total_ms += step_ms[-1]
         for i, k in enumerate(kernels):
             per_kernel[k] += e[i].elapsed_time(e[i + 1])
+            per_kernel_steps[k].append(e[i].elapsed_time(e[i + 1]))
     wall = time.perf_counter() - wall0
     time.sleep(0.2)
     clocks = sampler.stop()
@@ -266,8 +272,10 @@ def run_gpu(args):
     for k in kernels:
         us = per_kernel[k] / args.steps * 1e3
         gbs = alg[k] / (us * 1e-6) / 1e9
+        q = sorted(per_kernel_steps[k])
         breakdown[k] = {"us": round(us, 3), "algorithmic_bytes": alg[k], "achieved_gbs": round(gbs, 1),
-                        "hbm_frac": round(gbs / hbm_peak, 4), "share": round(per_kernel[k] / total_ms, 4)}
+                        "hbm_frac": round(gbs / hbm_peak, 4), "share": round(per_kernel[k] / total_ms, 4),
+                        "us_p10_p50_p90": [round(1e3 * q[int(f * (len(q) - 1))], 2) for f in (0.1, 0.5, 0.9)]}
     dominant = max(kernels, key=lambda k: per_kernel[k])
     sources = {"systematic": "pf_persistent.cu", "stratified": "pf_persistent.cu",
                "multinomial": "pf_persistent.cu", "metropolis": "pf_metropolis.cu", "gather": "pf_misc.cu",
@@ -304,6 +312,7 @@ def run_gpu(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 5),
+        "ms_per_step_p10_p50_p90": [round(sorted(step_ms)[int(f * (len(step_ms) - 1))], 5) for f in (0.1, 0.5, 0.9)],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
