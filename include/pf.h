@@ -263,7 +263,9 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream);
  * for P's size class and returns it in *min_tile_out (and its median time in
  * microseconds in *us_out; either may be NULL).  Synchronous; overwrites
  * `ancestors`; arguments as pf_resample_systematic, 1 <= reps <= 1000.
- * PF_ERR_INVALID while `stream` is capturing a graph.
+ * PF_ERR_INVALID while `stream` is capturing a graph.  While it runs, other
+ * calls of the same kind and size class on the device use the candidate being
+ * timed (their results stay correct; only their tiling differs).
  *
  * pf_set_min_tile stores a choice (e.g. one tuned in an earlier process;
  * 0 restores the default of 2048); pf_get_min_tile returns the value in
