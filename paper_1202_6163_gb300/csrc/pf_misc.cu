@@ -86,12 +86,13 @@ constexpr int kRedThreads = 256;
 constexpr int kRedPerThread = 16;
 constexpr int kRedTile = kRedThreads * kRedPerThread;
 
-struct RedRecord {
+struct RedRecord {  // 32 bytes, read back as two 16-byte halves
     int32_t k;
     float m;
     float s_hi, s_lo, q_hi, q_lo;
     uint32_t bad, pad;
 };
+static_assert(sizeof(RedRecord) == 32, "record layout");
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float w) {
     const float y = __fsub_rn(w, c);
@@ -197,10 +198,19 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict_
     const int T = gridDim.x;
     int kmax = INT_MIN, anybad = 0;
     float mmax = -INFINITY;
+    // each record as two 16-byte loads; the first one a thread reads stays in
+    // registers for the second pass (the only one when T <= kRedThreads)
+    const uint32_t* rw = reinterpret_cast<const uint32_t*>(rec);
+    uint4 r0 = make_uint4(0, 0, 0, 0), r1 = make_uint4(0, 0, 0, 0);
     for (int t = tid; t < T; t += kRedThreads) {
-        anybad |= (int)__ldcg(&rec[t].bad);
-        if (__ldcg(&rec[t].s_hi) > 0.f) kmax = max(kmax, __ldcg(&rec[t].k));
-        mmax = fmaxf(mmax, __ldcg(&rec[t].m));
+        const uint4 a = ld_cg_v4_u32(rw + 8 * t), b = ld_cg_v4_u32(rw + 8 * t + 4);
+        if (t == tid) {
+            r0 = a;
+            r1 = b;
+        }
+        anybad |= (int)b.z;
+        if (__uint_as_float(a.z) > 0.f) kmax = max(kmax, (int)a.x);
+        mmax = fmaxf(mmax, __uint_as_float(a.y));
     }
     kmax = warp_max_i(kmax);
     mmax = warp_max(mmax);
@@ -228,9 +238,14 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict_
     }
     i128 S = 0, Q = 0;
     for (int t = tid; t < T; t += kRedThreads) {
-        const int sh = __ldcg(&rec[t].k) - K;
-        S += fixed_of(__ldcg(&rec[t].s_hi), sh) + fixed_of(__ldcg(&rec[t].s_lo), sh);
-        Q += fixed_of(__ldcg(&rec[t].q_hi), 2 * sh) + fixed_of(__ldcg(&rec[t].q_lo), 2 * sh);
+        uint4 a = r0, b = r1;
+        if (t != tid) {
+            a = ld_cg_v4_u32(rw + 8 * t);
+            b = ld_cg_v4_u32(rw + 8 * t + 4);
+        }
+        const int sh = (int)a.x - K;
+        S += fixed_of(__uint_as_float(a.z), sh) + fixed_of(__uint_as_float(a.w), sh);
+        Q += fixed_of(__uint_as_float(b.x), 2 * sh) + fixed_of(__uint_as_float(b.y), 2 * sh);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
