@@ -97,8 +97,10 @@ __device__ bool carries(const SortedParams& p, PersistShared& sm, TableEntry* ta
     const uint32_t* rec = reinterpret_cast<const uint32_t*>(p.slots);
     // largest tile exponent among tiles with weight; NaN/+inf check
     int bad = 0, kmax = INT_MIN;
+    uint4 mine = make_uint4(0, 0, 0, 0xffffffffu);  // record `tid`, kept for the second pass
     for (int t = tid; t < T; t += kThreads) {
         const uint4 r = ld_cg_v4_u32(rec + 4 * t);
+        if (t == tid) mine = r;
         const float sh = __uint_as_float(r.y);
         bad |= !(sh <= 3.402823466e38f);
         if (sh > 0.f) kmax = max(kmax, (int)r.x);
@@ -118,7 +120,7 @@ __device__ bool carries(const SortedParams& p, PersistShared& sm, TableEntry* ta
     for (int base = 0; base < T; base += kThreads) {
         const int t = base + tid;
         uint4 r = make_uint4(0, 0, 0, 0xffffffffu);
-        if (t < T) r = ld_cg_v4_u32(rec + 4 * t);
+        if (t < T) r = base == 0 ? mine : ld_cg_v4_u32(rec + 4 * t);
         const int sh = (int)r.x - K;
         const i128 a = (t < T) ? fixed_of(__uint_as_float(r.y), sh) + fixed_of(__uint_as_float(r.z), sh) : (i128)0;
         const i128 B = running + block_scan_i128(sm, a);  // carry of tile t
