@@ -156,7 +156,8 @@ def run_gpu(args):
                "figure2": lambda: run_figure2(args, pf, torch, dev),
                "metropolis": lambda: run_metropolis_sweep(args, pf, torch, dev),
                "inplace": lambda: run_inplace(args, pf, torch, dev),
-               "sweep": lambda: run_size_sweep(args, pf, torch, dev, hbm_peak)}[args.only]()
+               "sweep": lambda: run_size_sweep(args, pf, torch, dev, hbm_peak),
+               "sorted": lambda: run_sorted_ablation(args, pf, torch, dev)}[args.only]()
         if rank == 0:
             print(json.dumps({"leg": args.only, **leg}))
         return
@@ -798,6 +799,57 @@ def run_size_sweep(args, pf, torch, dev, hbm_peak):
             "l2_random_reads_per_s": round(l2_rate, 1), "hbm_peak_gbs": hbm_peak, "rows": rows}
 
 
+def run_sorted_ablation(args, pf, torch, dev):
+    """The paper's remark on pre-sorting (Section 3: the binary search is faster
+    on sorted weights, but the sort costs more than it saves), re-tested here:
+    multinomial resampling of N(0, s^2) log-weights as given, against a
+    descending sort (torch.sort, a library sort: this is an ablation, not the
+    library's path) followed by multinomial resampling of the sorted weights
+    (ancestors then map back through the sort's index), with systematic
+    resampling for scale.  L2 flushed before each timed call."""
+    from paper_1202_6163_gb300 import workloads
+    s = torch.cuda.current_stream(dev)
+    stream = s.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            z.record(s)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(z) * 1e3)
+        return statistics.median(ts)
+
+    for k in (16, 20, 24):
+        P = 1 << k
+        pf.pf_reserve(P, 0, 0, stream)
+        for sp in (1.0, 3.0):
+            lw = torch.from_numpy(workloads.gaussian_logw(P, sp, seed=k)).to(dev)
+            anc = torch.empty(P, dtype=torch.int32, device=dev)
+            t_multi = timed(lambda: pf.pf_resample_multinomial(lw, P, 0, 1, anc, stream))
+            t_sys = timed(lambda: pf.pf_resample_systematic(lw, P, 0, 1, anc, stream))
+            with torch.cuda.stream(s):
+                srt, idx = torch.sort(lw, descending=True)
+                t_sort = timed(lambda: torch.sort(lw, descending=True))
+            t_multi_sorted = timed(lambda: pf.pf_resample_multinomial(srt, P, 0, 1, anc, stream))
+            with torch.cuda.stream(s):
+                t_map = timed(lambda: idx[anc.long()])
+            rows.append({"P": P, "s": sp, "multinomial_us": round(t_multi, 2), "systematic_us": round(t_sys, 2),
+                         "sort_us": round(t_sort, 2), "multinomial_sorted_us": round(t_multi_sorted, 2),
+                         "map_back_us": round(t_map, 2),
+                         "sorted_total_us": round(t_sort + t_multi_sorted + t_map, 2)})
+    if pf.pf_get_device_status(s) != pf.PF_OK:
+        raise RuntimeError("device status not OK in the sorting ablation")
+    return {"workload": "single filter, P = 2^16, 2^20, 2^24, log-weights N(0, s^2), s in {1, 3}", "rows": rows}
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_step_time(P, metro_chains, seed):
     """One step of the oracle over a bounded sample: the three cumulative resamplers, ESS
@@ -891,7 +943,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-bootstrap", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace", "sweep"],
+    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace", "sweep", "sorted"],
                     default=None,
                     help="run one secondary leg alone and print its JSON (for profiling)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
