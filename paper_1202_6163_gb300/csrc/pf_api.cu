@@ -214,11 +214,16 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     // multinomial: the tiles' cumulative weights (PA floats), then samples of
     // every 16th (c2) and 256th (c1) for the three-level draws, when the c1
     // samples fit in shared memory beside the tile table
-    int cpt2 = 0, cpt1 = 0;
+    int cpt2 = 0, cpt1 = 0, c1shift = 8;
     size_t c2_at = 0, c1_at = 0, mscratch = 0;
     if (kind == PF_MULTINOMIAL) {
+        // level-1 stride 2^c1shift >= 256: the smallest whose samples fit beside the table
         cpt2 = ((tile + 15) / 16 + 15) & ~15;
-        cpt1 = (tile + 255) / 256;
+        while ((1 << c1shift) < tile &&
+               (size_t)T * sizeof(float4) + (size_t)T * ((tile + (1 << c1shift) - 1) >> c1shift) * sizeof(float) >
+                   (size_t)kMaxTilesTotal * sizeof(float4))
+            ++c1shift;
+        cpt1 = (tile + (1 << c1shift) - 1) >> c1shift;
         if ((size_t)T * sizeof(float4) + (size_t)T * cpt1 * sizeof(float) > (size_t)kMaxTilesTotal * sizeof(float4))
             cpt1 = cpt2 = 0;
         c2_at = ((size_t)PA * sizeof(float) + 255) & ~(size_t)255;
@@ -249,6 +254,7 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     p.c1_out = cpt2 > 0 ? reinterpret_cast<float*>((char*)w->scratch + c1_at) : nullptr;
     p.cpt2 = cpt2;
     p.cpt1 = cpt1;
+    p.c1shift = c1shift;
     return cuda_fail(launch_sorted_persistent(kind, p, G, s), "persistent launch");
 }
 

@@ -421,15 +421,18 @@ __device__ __forceinline__ int window_below(const float* w, int n, float xh, flo
 }
 
 // Single-launch multinomial draw over three levels of the tiles' cumulative
-// weights: every 256th |v| of each tile (c1, shared memory), every 16th (c2,
-// global, cpt2 per tile, each tile's block 64-byte aligned) and v itself
-// (global).  Each level narrows to a window of 16 entries of the next, read
-// whole; the predicate and the monotone sequence are those of the plain
-// search, so the result is the same, with two dependent 64-byte reads per
-// draw instead of a dozen dependent 4-byte reads.
+// weights: every 2^c1shift-th |v| of each tile (c1, shared memory, c1shift >=
+// 8), every 16th (c2, global, cpt2 per tile, each tile's block 64-byte
+// aligned) and v itself (global).  Level 1 narrows to 2^(c1shift-4) samples of
+// c2; when that is more than 16, a binary search over their 16-entry blocks
+// (one 4-byte read a level) picks the block; each remaining level reads one
+// 16-entry window whole.  The predicate and the monotone sequence are those of
+// the plain search, so the result is the same, with two dependent 64-byte
+// reads per draw (plus c1shift - 8 small ones) instead of a dozen 4-byte ones.
 __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const TableEntry* table, int T, const float* v,
                                                            const float* c2, int cpt2, const float* c1, int cpt1,
-                                                           int tile, int64_t PA, int lead, float Wh, float Wl) {
+                                                           int c1shift, int tile, int64_t PA, int lead, float Wh,
+                                                           float Wl) {
     float uh, ul;
     u32_pair(x, uh, ul);
     const float th = __fmul_rn(uh, Wh);
@@ -451,8 +454,8 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
     }
     const int64_t b0 = (int64_t)lo * tile;
     const int nt = (int)min((int64_t)tile, PA - b0);
-    const int n2 = (nt + 15) >> 4, n1 = (nt + 255) >> 8;
-    // level 1: first 256-element window whose last sample is above the target
+    const int n2 = (nt + 15) >> 4, n1 = (nt + (1 << c1shift) - 1) >> c1shift;
+    // level 1: first window whose last sample is above the target
     const float* c = c1 + lo * cpt1;
     int cl = 0, cn = n1;
     while (cn > 0) {
@@ -466,12 +469,30 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
     }
     int idx = e.il;
     if (cl < n1) {
-        // level 2: the 16 samples of that window, then level 3: the 16 elements
-        const int m2 = (cl << 4) + window_below(c2 + (int64_t)lo * cpt2 + (cl << 4), min(16, n2 - (cl << 4)), xh, xl);
+        const float* c2t = c2 + (int64_t)lo * cpt2;
+        int m2 = cl << (c1shift - 4);  // first c2 sample of the window
+        if (c1shift > 8) {
+            // several 16-sample blocks: the first whose last sample is above the target
+            int bl = 0, bn = min(1 << (c1shift - 8), (n2 - m2 + 15) >> 4);
+            while (bn > 0) {
+                const int half = bn >> 1;
+                const int last = min(m2 + ((bl + half + 1) << 4), n2) - 1;
+                if (__fsub_rn(__ldcg(c2t + last), xh) > xl) {
+                    bn = half;
+                } else {
+                    bl += half + 1;
+                    bn -= half + 1;
+                }
+            }
+            m2 += bl << 4;
+        }
+        // level 2: the block of 16 samples, then level 3: the 16 elements
+        m2 += window_below(c2t + m2, min(16, n2 - m2), xh, xl);
         const int w0 = m2 << 4;
-        const int below = window_below(v + b0 + w0, min(16, nt - w0), xh, xl);
+        const int wn = min(16, nt - w0);
+        const int below = window_below(v + b0 + w0, wn, xh, xl);
         idx = w0 + below;
-        if (below >= min(16, nt - w0)) idx = e.il;  // not reached: the window's last sample is above the target
+        if (below >= wn) idx = e.il;  // not reached: the window's last sample is above the target
         else if (zero_flag(__ldcg(v + b0 + idx))) {  // rounding landed on a zero weight: the next positive one
             int f = e.il;
             for (int z = idx + 1; z < nt; ++z)
@@ -486,15 +507,16 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
 }
 
 // This thread's samples of its tile: every 16th |v| (and the tile's last)
-// into c2, every 256th (and the last) into c1.
-__device__ __forceinline__ void write_tile_samples(const TileThread& th, int n, float* c2, float* c1) {
+// into c2, every 2^c1shift-th (and the last) into c1.
+__device__ __forceinline__ void write_tile_samples(const TileThread& th, int n, float* c2, float* c1, int c1shift) {
+    const int m1 = (1 << c1shift) - 1;
 #pragma unroll
     for (int i = 0; i < kMaxPerThread; ++i) {
         const int e = th.e0 + i;
         if (i < th.K && e < n) {
             const bool lastel = e == n - 1;
             if (((e + 1) & 15) == 0 || lastel) c2[e >> 4] = fabsf(th.v[i]);
-            if (((e + 1) & 255) == 0 || lastel) c1[e >> 8] = fabsf(th.v[i]);
+            if (((e + 1) & m1) == 0 || lastel) c1[e >> c1shift] = fabsf(th.v[i]);
         }
     }
 }

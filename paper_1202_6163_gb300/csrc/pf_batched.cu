@@ -76,6 +76,7 @@ __device__ __forceinline__ void filter_params(const BatchParams& bp, int f, int6
     p.c2_out = nullptr;
     p.c1_out = nullptr;
     p.cpt2 = p.cpt1 = 0;
+    p.c1shift = 8;
 }
 
 // Warp 0: the exact fixed-point carries of a filter's Tf tiles from their

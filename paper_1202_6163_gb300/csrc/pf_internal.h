@@ -63,8 +63,8 @@ struct SortedParams {
     float* v_out;     // multinomial: tile-local cumulative weights (P + lead floats), else null
     int lead;         // elements of the aligned window before element 0 (0..3)
     float* c2_out;    // multinomial: every 16th |v| of each tile (cpt2 per tile), or null
-    float* c1_out;    // multinomial: every 256th |v| of each tile (cpt1 per tile)
-    int cpt2, cpt1;
+    float* c1_out;    // multinomial: every 2^c1shift-th |v| of each tile (cpt1 per tile)
+    int cpt2, cpt1, c1shift;
 };
 
 // Batched call: F filters, filter f owns lw[offsets[f] .. offsets[f+1]).

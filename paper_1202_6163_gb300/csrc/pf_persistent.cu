@@ -169,8 +169,8 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
         if (p.c2_out) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                a[s] = multinomial_draw_3level(word_of(r, s), table, T, p.v_out, p.c2_out, p.cpt2, c1, p.cpt1, p.tile,
-                                               p.P + p.lead, p.lead, Wh, Wl);
+                a[s] = multinomial_draw_3level(word_of(r, s), table, T, p.v_out, p.c2_out, p.cpt2, c1, p.cpt1,
+                                               p.c1shift, p.tile, p.P + p.lead, p.lead, Wh, Wl);
         } else {
             multinomial_draws4<false>(r, table, T, p.v_out, p.tile, p.P + p.lead, p.lead, Wh, Wl, a);
         }
@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
         if (KIND == KIND_MULTI) {
             write_tile_v(p, th, t0, n);
-            if (p.c2_out) write_tile_samples(th, n, p.c2_out + (int64_t)t * p.cpt2, p.c1_out + (int64_t)t * p.cpt1);
+            if (p.c2_out)
+                write_tile_samples(th, n, p.c2_out + (int64_t)t * p.cpt2, p.c1_out + (int64_t)t * p.cpt1, p.c1shift);
             __threadfence();
         }
         if (tid == 0) {
