@@ -53,7 +53,7 @@ static cudaError_t gather_vt(const void* src, int64_t P_src, int64_t row_bytes, 
     const int64_t vecs = row_bytes / (int64_t)sizeof(VT);
     const int64_t total = P_dst * vecs;
     int64_t blocks = (total + (int64_t)kGatherThreads * kUnroll - 1) / ((int64_t)kGatherThreads * kUnroll);
-    const int64_t cap = (int64_t)num_sms * 16;
+    const int64_t cap = (int64_t)num_sms * 8;  // one resident wave (8 CTAs of 256 threads per SM)
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     const bool pow2 = (vecs & (vecs - 1)) == 0;
