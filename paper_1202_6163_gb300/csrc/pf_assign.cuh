@@ -86,7 +86,7 @@ __device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i,
 // over the chunk fills every run.  Chunk slot s sits at out[s + shift] so that
 // out[x] maps to the 16-byte aligned global position gb + x; each thread scans
 // and stores S consecutive entries (S * kThreads >= c1 - c0 + shift).
-template <int S>
+template <int S, int KK = 0>  // KK: elements per thread when fixed, 0 = th.K
 __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared& sm, int32_t* out,
                                              const TileThread& th, long long jlo, int c0, int c1, int shift,
                                              int start0, int32_t base) {
@@ -97,8 +97,8 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
     __syncthreads();
     int a = start0;
 #pragma unroll
-    for (int i = 0; i < kMaxPerThread; ++i) {
-        if (i < th.K && ((th.pos >> i) & 1u)) {
+    for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
+        if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
             const int b = __float_as_int(th.v[i]);
             if (b > a) {
                 if (a >= c0 && a < c1) out[a - c0 + shift] = base + i;
@@ -151,7 +151,7 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
     __syncthreads();
 }
 
-template <int KIND>
+template <int KIND, int KK = 0>  // KK: elements per thread when fixed, 0 = th.K
 __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_t* out, TileThread& th,
                                  const TileSummary& ts, int64_t index0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -163,8 +163,8 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
     u32x4 cw = {0, 0, 0, 0};
     int last_n = -1;
 #pragma unroll
-    for (int i = 0; i < kMaxPerThread; ++i) {
-        if (i < th.K && ((th.pos >> i) & 1u)) {
+    for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
+        if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
             int n;
             if (th.e0 + i == ts.i_last) {
                 n = noff;
@@ -217,11 +217,11 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
         const int shift = (int)(((uintptr_t)(p.anc + jlo + c0) >> 2) & 3u);  // to a 16-byte boundary
         const int need = c1 - c0 + shift;
         if (need <= 4 * kThreads)
-            decode_chunk<4>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+            decode_chunk<4, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
         else if (need <= 8 * kThreads)
-            decode_chunk<8>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+            decode_chunk<8, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
         else
-            decode_chunk<16>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+            decode_chunk<16, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
     }
 }
 
@@ -508,12 +508,13 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
 
 // This thread's samples of its tile: every 16th |v| (and the tile's last)
 // into c2, every 2^c1shift-th (and the last) into c1.
+template <int KK = 0>
 __device__ __forceinline__ void write_tile_samples(const TileThread& th, int n, float* c2, float* c1, int c1shift) {
     const int m1 = (1 << c1shift) - 1;
 #pragma unroll
-    for (int i = 0; i < kMaxPerThread; ++i) {
+    for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
         const int e = th.e0 + i;
-        if (i < th.K && e < n) {
+        if ((KK || i < th.K) && e < n) {
             const bool lastel = e == n - 1;
             if (((e + 1) & 15) == 0 || lastel) c2[e >> 4] = fabsf(th.v[i]);
             if (((e + 1) & m1) == 0 || lastel) c1[e >> c1shift] = fabsf(th.v[i]);
@@ -555,11 +556,12 @@ __device__ __forceinline__ void read_tile_v(const float* vg0, int n, TileThread&
 }
 
 // The tile's cumulative weights to global memory (sign bit: zero weight), for the searches.
+template <int KK = 0>
 __device__ __forceinline__ void write_tile_v(const SortedParams& p, const TileThread& th, int64_t t0, int n) {
     float* vg = p.v_out + t0 + th.e0;
 #pragma unroll
-    for (int q = 0; q < kMaxPerThread / 4; ++q) {
-        if (4 * q < th.K) {
+    for (int q = 0; q < (KK ? KK : kMaxPerThread) / 4; ++q) {
+        if (KK || 4 * q < th.K) {
             float o[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {

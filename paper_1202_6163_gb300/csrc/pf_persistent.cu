@@ -184,7 +184,8 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
     }
 }
 
-template <int KIND>
+// KK: elements per thread of a full tile (4, 8 or 16; the host picks it from p.tile).
+template <int KIND, int KK>
 __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
@@ -208,12 +209,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         const int t = t_first + r;
         const int64_t t0 = (int64_t)t * p.tile;
         const int n = (int)min((int64_t)p.tile, PA - t0);
-        ts = tile_scan(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
+        ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
         if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
         if (KIND == KIND_MULTI) {
-            write_tile_v(p, th, t0, n);
+            write_tile_v<KK>(p, th, t0, n);
             if (p.c2_out)
-                write_tile_samples(th, n, p.c2_out + (int64_t)t * p.cpt2, p.c1_out + (int64_t)t * p.cpt1, p.c1shift);
+                write_tile_samples<KK>(th, n, p.c2_out + (int64_t)t * p.cpt2, p.c1_out + (int64_t)t * p.cpt1, p.c1shift);
             __threadfence();
         }
         if (tid == 0) {
@@ -246,20 +247,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         const int t = t_first + r;
         const int64_t t0 = (int64_t)t * p.tile;
         if (r != t_count - 1)
-            ts = tile_scan(p.lw + t0, t == 0 ? p.lead : 0, (int)min((int64_t)p.tile, PA - t0), sm.tile, th);
+            ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, (int)min((int64_t)p.tile, PA - t0), sm.tile, th);
         if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], ts.k);
         __syncthreads();
-        assign_offspring<KIND>(p, sm.as, out, th, ts, t0 - p.lead);
+        assign_offspring<KIND, KK>(p, sm.as, out, th, ts, t0 - p.lead);
     }
 }
 
-template <int KIND>
+template <int KIND, int KK>
 static cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(k_persistent<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_persistent<KIND, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)persistent_smem_bytes(KIND, kMaxTilesTotal));
 }
 
-template <int KIND>
+template <int KIND, int KK>
 static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -272,43 +273,58 @@ static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_persistent<KIND>, p);
+    return cudaLaunchKernelEx(&cfg, k_persistent<KIND, KK>, p);
+}
+
+template <int KIND>
+static cudaError_t launch_k(const SortedParams& p, int grid, cudaStream_t s) {
+    const int q = (p.tile + kThreads - 1) / kThreads;  // elements per thread of a full tile
+    if (q <= 4) return launch_kind<KIND, 4>(p, grid, s);
+    if (q <= 8) return launch_kind<KIND, 8>(p, grid, s);
+    return launch_kind<KIND, 16>(p, grid, s);
 }
 
 cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s) {
     const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
-    if (p.n_tiles < 1 || p.n_tiles > kMaxTilesTotal || R > kMaxOwn || (int64_t)grid * R < p.n_tiles)
+    if (p.n_tiles < 1 || p.n_tiles > kMaxTilesTotal || R > kMaxOwn || (int64_t)grid * R < p.n_tiles ||
+        p.tile < 4 || p.tile > kTileMax)
         return cudaErrorInvalidValue;
     switch (kind) {
-    case KIND_MULTI: return launch_kind<KIND_MULTI>(p, grid, s);
-    case KIND_STRAT: return launch_kind<KIND_STRAT>(p, grid, s);
-    case KIND_SYS: return launch_kind<KIND_SYS>(p, grid, s);
+    case KIND_MULTI: return launch_k<KIND_MULTI>(p, grid, s);
+    case KIND_STRAT: return launch_k<KIND_STRAT>(p, grid, s);
+    case KIND_SYS: return launch_k<KIND_SYS>(p, grid, s);
     }
     return cudaErrorInvalidValue;
 }
 
-// Called once per device: raises the dynamic shared memory limit and returns
-// how many CTAs of the kind fit on one SM (the cooperative grid limit), at the
-// largest shared-memory size a launch may ask for.
+// Resident CTAs per SM of kind's kernels at the largest shared-memory size a
+// launch may ask for (the smallest over the three per-thread widths; raises
+// their dynamic shared memory limits on the way).  Called once per device.
+template <int KIND>
+static int blocks_per_sm_kind() {
+    const size_t smem = persistent_smem_bytes(KIND, kMaxTilesTotal);
+    int best = INT_MAX, nb = 0;
+    if (set_smem_attr<KIND, 4>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, 4>, kThreads, smem) != cudaSuccess)
+        return 0;
+    best = min(best, nb);
+    if (set_smem_attr<KIND, 8>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, 8>, kThreads, smem) != cudaSuccess)
+        return 0;
+    best = min(best, nb);
+    if (set_smem_attr<KIND, 16>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, 16>, kThreads, smem) != cudaSuccess)
+        return 0;
+    return min(best, nb);
+}
+
 int persistent_blocks_per_sm(int kind) {
-    int nb = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    const size_t smem = persistent_smem_bytes(kind, kMaxTilesTotal);
     switch (kind) {
-    case KIND_MULTI:
-        if (set_smem_attr<KIND_MULTI>() == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND_MULTI>, kThreads, smem);
-        break;
-    case KIND_STRAT:
-        if (set_smem_attr<KIND_STRAT>() == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND_STRAT>, kThreads, smem);
-        break;
-    case KIND_SYS:
-        if (set_smem_attr<KIND_SYS>() == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND_SYS>, kThreads, smem);
-        break;
+    case KIND_MULTI: return blocks_per_sm_kind<KIND_MULTI>();
+    case KIND_STRAT: return blocks_per_sm_kind<KIND_STRAT>();
+    case KIND_SYS: return blocks_per_sm_kind<KIND_SYS>();
     }
-    return e == cudaSuccess ? nb : 0;
+    return 0;
 }
 
 }  // namespace pf

@@ -48,14 +48,15 @@ __device__ __forceinline__ int per_thread_count(int n) {
 
 __device__ __forceinline__ bool zero_flag(float v) { return __float_as_uint(v) >> 31; }
 
-// Loads this thread's K elements (tile-local e0 .. e0+K) of base[lo..n); base is
-// 16-byte aligned.  Slots outside [lo, n) read as -inf (zero weight).
-__device__ __forceinline__ void tile_load(const float* __restrict__ base, int lo, int n, int e0, int K,
-                                          float (&x)[kMaxPerThread]) {
+// Loads this thread's KK elements (tile-local e0 .. e0+KK) of base[lo..n);
+// base is 16-byte aligned.  Slots outside [lo, n) read as -inf (zero weight).
+template <int KK>
+__device__ __forceinline__ void tile_load_k(const float* __restrict__ base, int lo, int n, int e0,
+                                            float (&x)[kMaxPerThread]) {
 #pragma unroll
-    for (int q = 0; q < kMaxPerThread / 4; ++q) {
+    for (int q = 0; q < KK / 4; ++q) {
         const int idx = e0 + 4 * q;
-        if (4 * q < K && idx >= lo && idx + 3 < n) {
+        if (idx >= lo && idx + 3 < n) {
             const float4 v = __ldg(reinterpret_cast<const float4*>(base + idx));
             x[4 * q + 0] = v.x;
             x[4 * q + 1] = v.y;
@@ -63,8 +64,7 @@ __device__ __forceinline__ void tile_load(const float* __restrict__ base, int lo
             x[4 * q + 3] = v.w;
         } else {
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                x[4 * q + r] = (4 * q < K && idx + r >= lo && idx + r < n) ? __ldg(base + idx + r) : -INFINITY;
+            for (int r = 0; r < 4; ++r) x[4 * q + r] = (idx + r >= lo && idx + r < n) ? __ldg(base + idx + r) : -INFINITY;
         }
     }
 }
@@ -72,24 +72,25 @@ __device__ __forceinline__ void tile_load(const float* __restrict__ base, int lo
 // Block-wide; every thread of the CTA must call it.  Scans base[0..n) with the
 // first `lo` slots taken as zero weights; fills th (this thread's elements) and
 // returns the tile summary (identical in every thread).
-__device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base, int lo, int n, TileShared& sm,
-                                                 TileThread& th) {
+// KK elements per thread (n <= KK * kThreads); tile_scan picks KK from n.
+template <int KK>
+__device__ __forceinline__ TileSummary tile_scan_k(const float* __restrict__ base, int lo, int n, TileShared& sm,
+                                                   TileThread& th) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = per_thread_count(n);
-    const int e0 = tid * K;
-    th.K = K;
+    const int e0 = tid * KK;
+    th.K = KK;
     th.e0 = e0;
 
     if (tid == 0) sm.i_last = -1;
 
     float* x = th.v;
-    tile_load(base, lo, n, e0, K, th.v);
+    tile_load_k<KK>(base, lo, n, e0, th.v);
 
     // 1. tile maximum and domain check
     float m = -INFINITY;
     int bad = 0;
 #pragma unroll
-    for (int i = 0; i < kMaxPerThread; ++i) {
+    for (int i = 0; i < KK; ++i) {
         bad |= !(x[i] <= 3.402823466e38f);  // NaN or +inf
         m = fmaxf(m, x[i]);
     }
@@ -107,19 +108,17 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
     int p = -1;
     uint32_t posbits = 0;
 #pragma unroll
-    for (int i = 0; i < kMaxPerThread; ++i) {
-        if (i < K) {
-            const float w = weight_rel(x[i], R);
-            if (w > 0.f) {
-                p = i;
-                posbits |= 1u << i;
-            }
-            const float y = __fsub_rn(w, c);
-            const float t = __fadd_rn(s, y);
-            c = __fsub_rn(__fsub_rn(t, s), y);
-            s = t;
-            x[i] = s;
+    for (int i = 0; i < KK; ++i) {
+        const float w = weight_rel(x[i], R);
+        if (w > 0.f) {
+            p = i;
+            posbits |= 1u << i;
         }
+        const float y = __fsub_rn(w, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+        x[i] = s;
     }
     th.pos = posbits;
 
@@ -151,7 +150,7 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
     // 4. tile-local cumulative weights; elements from the last positive one on
     // take the next base so that no gap is left between threads
 #pragma unroll
-    for (int i = 0; i < kMaxPerThread; ++i) x[i] = (i >= p) ? Vn : fminf(__fadd_rn(Vk, x[i]), Vn);
+    for (int i = 0; i < KK; ++i) x[i] = (i >= p) ? Vn : fminf(__fadd_rn(Vk, x[i]), Vn);
 
     TileSummary ts;
     ts.k = k;
@@ -159,6 +158,15 @@ __device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base,
     ts.i_last = sm.i_last;
     ts.bad = bad;
     return ts;
+}
+
+// Block-wide; KK from the tile length (4, 8 or 16 elements per thread).
+__device__ __forceinline__ TileSummary tile_scan(const float* __restrict__ base, int lo, int n, TileShared& sm,
+                                                 TileThread& th) {
+    const int K = per_thread_count(n);
+    if (K == 4) return tile_scan_k<4>(base, lo, n, sm, th);
+    if (K == 8) return tile_scan_k<8>(base, lo, n, sm, th);
+    return tile_scan_k<16>(base, lo, n, sm, th);
 }
 
 }  // namespace pf
