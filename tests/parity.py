@@ -99,26 +99,29 @@ def check_cumulative(kind: str, lw, a_gpu, a_orc, seed: int = 0, filter_id: int 
 
 def _replay(lw64, P, k, props, unifs, b0, flips_left, target, tau):
     """Depth-first replay of a chain from step b0 in state k; True if target is reachable
-    by flipping at most flips_left near-tie decisions."""
+    by flipping at most flips_left near-tie decisions.  The threshold of every step is
+    r = exp(lw_j - lw_k), including r >= 1 (a move the exact rule always takes is a near
+    tie when u lies within tau r of r, i.e. when r < 1 / (1 - tau))."""
     for b in range(b0, len(props)):
         j = int(props[b])
         u = float(unifs[b])
-        if lw64[j] >= lw64[k]:
-            k = j
-            continue
-        r = math.exp(lw64[j] - lw64[k])
-        acc = u < r
-        if flips_left > 0 and abs(u - r) <= tau * r:
-            alt = k if acc else j
-            if _replay(lw64, P, alt, props, unifs, b + 1, flips_left - 1, target, tau):
-                return True
+        d = lw64[j] - lw64[k]  # +inf (state of zero weight), -inf (proposal of zero weight) or nan (both)
+        acc = bool(lw64[j] >= lw64[k]) or u < math.exp(d)
+        if flips_left > 0 and math.isfinite(d) and d < 1e-3:
+            r = math.exp(d)
+            if abs(u - r) <= tau * r:
+                alt = k if acc else j
+                if _replay(lw64, P, alt, props, unifs, b + 1, flips_left - 1, target, tau):
+                    return True
         if acc:
             k = j
     return k == target
 
 
-def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TAU, max_flips=3) -> ParityReport:
-    """a_gpu, a_orc: ancestors of the chains listed in `chains` (all chains if None)."""
+def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TAU, max_flips=3,
+                     draws=None) -> ParityReport:
+    """a_gpu, a_orc: ancestors of the chains listed in `chains` (all chains if None).
+    draws: (proposals, uniforms), each of shape (P, B), in place of the library's streams."""
     lw = np.asarray(lw, dtype=np.float32)
     lw64 = lw.astype(np.float64)
     P = lw.size
@@ -133,7 +136,10 @@ def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TA
     rep.mismatches = int(mism.size)
     for q in mism:
         i = int(idx[q])
-        props, unifs = oracle.metropolis_draws(seed, filter_id, P, i, B)
+        if draws is None:
+            props, unifs = oracle.metropolis_draws(seed, filter_id, P, i, B)
+        else:
+            props, unifs = draws[0][i], draws[1][i]
         ok = _replay(lw64, P, i, props, unifs, 0, max_flips, int(a_gpu[q]), tau)
         (rep.excused if ok else rep.failures).append((i, int(a_gpu[q]), int(a_orc[q])))
     return rep

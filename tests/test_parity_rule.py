@@ -63,3 +63,22 @@ def test_metropolis_wrong_chain_fails():
     rep = check_metropolis(lw, 16, bad, a, 9)
     assert not rep.ok and rep.mismatches == 1
     assert check_metropolis(lw, 16, a, a, 9).ok
+
+
+def test_metropolis_declined_move_to_a_barely_heavier_particle_is_a_near_tie():
+    # chain 0 proposes particle 1, whose log-weight is two float ulps above its own:
+    # r = exp(lw_1 - lw_0) = 1 + 2.4e-7 and u = 1 - 2^-24 lies within 1e-6 r of r, so a
+    # GPU that rounds the ratio below u and stays at 0 is excused; 1e-5 above is not
+    base = np.float32(1.0)
+    for step, ok in ((2, True), (84, False)):
+        lw = np.array([base, np.nextafter(base, np.float32(2), dtype=np.float32), 0.0, 0.0], np.float32)
+        for _ in range(step - 1):
+            lw[1] = np.nextafter(lw[1], np.float32(2), dtype=np.float32)
+        prop = np.array([[1], [1], [2], [3]], np.int32)
+        unif = np.full((4, 1), 1.0 - 2.0 ** -24)
+        a_orc = oracle.metropolis_u(lw, 1, prop, unif)
+        assert a_orc[0] == 1
+        a_gpu = a_orc.copy()
+        a_gpu[0] = 0
+        rep = check_metropolis(lw, 1, a_gpu, a_orc, 0, draws=(prop, unif))
+        assert rep.ok == ok and rep.mismatches == 1
