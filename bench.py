@@ -339,6 +339,8 @@ def run_gpu(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
+        if batched is not None:
+            out["cpu_baseline"]["batched"] = cpu_baseline_batched()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -890,6 +892,42 @@ def cpu_baseline(args, budget_s=None):
             "sample": f"{n} oracle steps at P=2^20: ess, systematic, stratified, multinomial and the gather "
                       f"in full; Metropolis (B={METRO_B}) on {chains} of the P chains, scaled to P",
             "s_per_step": round(per_step, 4)}
+
+
+def cpu_baseline_batched():
+    """The oracle on the whole 4096-filter workload of the batched leg (every
+    filter, each resampler), filters spread over all host cores by threads:
+    the oracle's C calls release the interpreter lock, so the threads run in
+    parallel.  Filter f uses key seeds[f] and Philox filter id f, as the
+    batched call does."""
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_1202_6163_gb300 import workloads
+    oracle.build()
+    F = 4096
+    off, sf = workloads.batched_layout(F=F, seed=0)
+    lw = workloads.batched_logw(off, sf, seed=0)
+    seeds = workloads.batched_seeds(F, base=0)
+    cores = os.cpu_count() or 1
+    calls = {"systematic": lambda x, sd, f: oracle.systematic(x, sd, f),
+             "stratified": lambda x, sd, f: oracle.stratified(x, sd, f),
+             "multinomial": lambda x, sd, f: oracle.multinomial(x, sd, f),
+             "metropolis": lambda x, sd, f: oracle.metropolis(x, METRO_B, sd, f)}
+    order = sorted(range(F), key=lambda f: -(off[f + 1] - off[f]))  # largest first, as the GPU plan
+    by_kind = {}
+    with cf.ThreadPoolExecutor(cores) as ex:
+        for name, fn in calls.items():
+            def one(f, fn=fn):
+                fn(lw[off[f]:off[f + 1]], int(seeds[f]), f)
+            t0 = time.perf_counter()
+            list(ex.map(one, order))
+            dt = time.perf_counter() - t0
+            by_kind[name] = {"s": round(dt, 3), "filters_per_s": round(F / dt, 1)}
+    return {"value": by_kind["systematic"]["filters_per_s"], "unit": "filters/s", "cores": cores, "kind": "oracle",
+            "sample": f"all {F} filters of the batched leg ({int(off[-1])} particles), largest first over "
+                      f"{cores} threads; Metropolis B={METRO_B}",
+            "by_kind": by_kind}
 
 
 def run_reference(args):

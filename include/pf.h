@@ -134,7 +134,10 @@ pf_status pf_resample_multinomial(const float* logw, int64_t P, int B, uint64_t 
  * takes B steps; step b proposes j uniformly over all P indices (a proposal of
  * k itself changes nothing) and moves to it when lw_j >= lw_k or when
  * u_b < exp(lw_j - lw_k).  a_i is the chain's final state.  No sum of weights
- * is formed.
+ * is formed.  For P <= 49152 (a batched filter: P_f <= 57344) the weights
+ * w = exp(lw - max lw) are staged in shared memory and a step moves when
+ * u_b w_k < w_j, which differs from the rule above only where u_b lies within
+ * 7e-7 (relative) of exp(lw_j - lw_k); larger P uses the rule as written.
  *   B > 0   number of steps;  B == 0 gives a_i = i;
  *   B < 0   B is chosen on the device from the bound of Eqs. 1-5 with
  *           eps = 0.01 and the actual w_max (see pf_metropolis_B), capped at

@@ -4,9 +4,17 @@
 // all P indices and moving to it when lw_j >= lw_k or when u < exp(lw_j - lw_k).
 // No sum of weights is formed, so there is no collective step and one launch
 // suffices.  Each Philox-4x32-10 call supplies the (proposal, uniform) pairs of
-// two consecutive steps.  The log-weights are read either from shared memory
-// (a CTA-wide copy, when P floats fit) or through L2 (ld.global.nc), where a
-// 4 MiB vector of P = 2^20 log-weights stays resident.
+// two consecutive steps.
+//
+// When the P weights fit shared memory, each CTA stages them once as
+// w_i = exp(lw_i - m) (m the largest log-weight, the subtraction error-free)
+// and a step accepts when u w_k < w_j: one product instead of an exponential
+// per step.  Each w carries at most 2.5 ulp of error (expf's 2 ulp and one
+// rounding), so the decision can differ from the exact rule only where u lies
+// within 7e-7 r of r = exp(lw_j - lw_k).  A state whose weight is below 2^-100
+// (zero, or too small for the product to stay a normal float) decides in log
+// space from the global log-weights instead.  Larger P reads the log-weights
+// through L2 (ld.global.nc), where the 4 MiB of P = 2^20 stays resident.
 #include "pf_device.cuh"
 
 namespace pf {
@@ -29,10 +37,8 @@ __device__ __forceinline__ bool metropolis_accept(float lj, float lk, float u) {
 // issues all their log-weight loads before resolving the steps in order.
 constexpr int kAhead = 8;
 
-template <bool STAGED>
-__device__ __forceinline__ void run_chain(const float* __restrict__ lw, const float* wsm, uint32_t Pu, uint32_t i,
-                                          int steps, uint32_t filter, uint32_t key0, uint32_t key1, uint32_t& k,
-                                          float& lk) {
+__device__ __forceinline__ void run_chain(const float* __restrict__ lw, uint32_t Pu, uint32_t i, int steps,
+                                          uint32_t filter, uint32_t key0, uint32_t key1, uint32_t& k, float& lk) {
     for (int b0 = 0; b0 < steps; b0 += kAhead) {
         uint32_t jj[kAhead];
         float uu[kAhead], ll[kAhead];
@@ -45,7 +51,7 @@ __device__ __forceinline__ void run_chain(const float* __restrict__ lw, const fl
             uu[2 * q + 1] = u23f(r.w);
         }
 #pragma unroll
-        for (int s = 0; s < kAhead; ++s) ll[s] = STAGED ? wsm[jj[s]] : __ldg(lw + jj[s]);
+        for (int s = 0; s < kAhead; ++s) ll[s] = __ldg(lw + jj[s]);
 #pragma unroll
         for (int s = 0; s < kAhead; ++s) {
             if (b0 + s < steps && metropolis_accept(ll[s], lk, uu[s])) {
@@ -56,31 +62,100 @@ __device__ __forceinline__ void run_chain(const float* __restrict__ lw, const fl
     }
 }
 
+// B steps of chain i from state k over staged weights w (shared memory).
+constexpr float kWeightFloor = 0x1p-100f;
+
+__device__ __forceinline__ void run_chain_w(const float* __restrict__ lw, const float* w, uint32_t Pu, uint32_t i,
+                                            int steps, uint32_t filter, uint32_t key0, uint32_t key1, uint32_t& k) {
+    float wk = w[k];
+    for (int b0 = 0; b0 < steps; b0 += kAhead) {
+        uint32_t jj[kAhead];
+        float uu[kAhead], ww[kAhead];
+#pragma unroll
+        for (int q = 0; q < kAhead / 2; ++q) {
+            const u32x4 r = philox(i, (uint32_t)((b0 >> 1) + q), filter, TAG_METRO, key0, key1);
+            jj[2 * q] = draw_index(r.x, Pu);
+            uu[2 * q] = u23f(r.y);
+            jj[2 * q + 1] = draw_index(r.z, Pu);
+            uu[2 * q + 1] = u23f(r.w);
+        }
+#pragma unroll
+        for (int s = 0; s < kAhead; ++s) ww[s] = w[jj[s]];
+#pragma unroll
+        for (int s = 0; s < kAhead; ++s) {
+            if (b0 + s < steps) {
+                const bool acc = wk >= kWeightFloor ? __fmul_rn(uu[s], wk) < ww[s]
+                                                    : metropolis_accept(__ldg(lw + jj[s]), __ldg(lw + k), uu[s]);
+                if (acc) {
+                    k = jj[s];
+                    wk = ww[s];
+                }
+            }
+        }
+    }
+}
+
+// Block-wide: copy lw[0..n) to w[] as weights exp(lw - m), m = max lw (0 when
+// every weight is zero); records PF_ERR_DOMAIN for a NaN or +inf log-weight.
+template <int THREADS>
+__device__ void stage_weights(const float* __restrict__ lw, int64_t n, float* w, float* red, uint32_t* ctl) {
+    const int tid = threadIdx.x;
+    float m = -INFINITY;
+    int bad = 0;
+    if ((((uintptr_t)lw) & 15u) == 0) {
+        const int64_t n4 = n >> 2;
+        for (int64_t q = tid; q < n4; q += THREADS) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(lw) + q);
+            reinterpret_cast<float4*>(w)[q] = v;
+            m = fmaxf(fmaxf(m, fmaxf(v.x, v.y)), fmaxf(v.z, v.w));
+            bad |= !(v.x <= 3.402823466e38f) | !(v.y <= 3.402823466e38f) | !(v.z <= 3.402823466e38f) |
+                   !(v.w <= 3.402823466e38f);
+        }
+        for (int64_t q = 4 * n4 + tid; q < n; q += THREADS) {
+            const float x = __ldg(lw + q);
+            w[q] = x;
+            m = fmaxf(m, x);
+            bad |= !(x <= 3.402823466e38f);
+        }
+    } else {
+        for (int64_t q = tid; q < n; q += THREADS) {
+            const float x = __ldg(lw + q);
+            w[q] = x;
+            m = fmaxf(m, x);
+            bad |= !(x <= 3.402823466e38f);
+        }
+    }
+    m = warp_max(m);
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    bad = __syncthreads_or(bad);
+    if (bad && tid == 0) set_status(ctl + CTL_STATUS, ST_DOMAIN);
+    float mt = red[0];
+#pragma unroll
+    for (int q = 1; q < THREADS / 32; ++q) mt = fmaxf(mt, red[q]);
+    const fpair R = {mt > -INFINITY ? mt : 0.f, 0.f};
+    for (int64_t q = tid; q < n; q += THREADS) w[q] = weight_rel(w[q], R);
+    __syncthreads();
+}
+
 template <bool STAGED>
 __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __restrict__ lw, int64_t P, int B,
                                                               const uint32_t* __restrict__ B_dev, uint32_t key0,
                                                               uint32_t key1, uint32_t filter,
                                                               int32_t* __restrict__ anc, uint32_t* ctl) {
     extern __shared__ float wsm[];
-    if (STAGED) {
-        // the whole log-weight vector: 16-byte copies when lw is 16-byte aligned
-        if ((((uintptr_t)lw) & 15u) == 0) {
-            const int n4 = (int)(P >> 2);
-            for (int q = threadIdx.x; q < n4; q += blockDim.x)
-                reinterpret_cast<float4*>(wsm)[q] = __ldg(reinterpret_cast<const float4*>(lw) + q);
-            for (int q = 4 * n4 + threadIdx.x; q < P; q += blockDim.x) wsm[q] = __ldg(lw + q);
-        } else {
-            for (int q = threadIdx.x; q < P; q += blockDim.x) wsm[q] = __ldg(lw + q);
-        }
-        __syncthreads();
-    }
+    __shared__ float red[kMetroThreads / 32];
+    if (STAGED) stage_weights<kMetroThreads>(lw, P, wsm, red, ctl);  // every CTA: the whole vector
     const int steps = B_dev ? (int)__ldg(B_dev) : B;
     const uint32_t Pu = (uint32_t)P;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        float lk = STAGED ? wsm[i] : __ldg(lw + i);
-        if (!(lk <= 3.402823466e38f)) set_status(ctl + CTL_STATUS, ST_DOMAIN);  // NaN or +inf
         uint32_t k = (uint32_t)i;
-        run_chain<STAGED>(lw, wsm, Pu, (uint32_t)i, steps, filter, key0, key1, k, lk);
+        if (STAGED) {
+            run_chain_w(lw, wsm, Pu, (uint32_t)i, steps, filter, key0, key1, k);
+        } else {
+            float lk = __ldg(lw + i);
+            if (!(lk <= 3.402823466e38f)) set_status(ctl + CTL_STATUS, ST_DOMAIN);  // NaN or +inf
+            run_chain(lw, Pu, (uint32_t)i, steps, filter, key0, key1, k, lk);
+        }
         anc[i] = (int32_t)k;
     }
 }
@@ -114,14 +189,18 @@ cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t*
 // ---------------------------------------------------------------------------
 // Batched: each CTA takes whole filters from a ticket counter, copies the
 // filter's log-weights to shared memory when they fit, and runs its chains
-// (filter-local indices, Philox filter id f, key seeds[f]).
+// (filter-local indices, Philox filter id f, key seeds[f]).  One 1024-thread
+// CTA per SM stages up to 56 Ki log-weights (224 KiB): a staged chain step is
+// bound by its Philox and acceptance arithmetic, an unstaged one by random
+// L2 reads, which sustain fewer steps per second.
 // ---------------------------------------------------------------------------
-constexpr int kMetroBThreads = 512;
-constexpr int kMetroBStage = 24 * 1024;  // floats staged per CTA (96 KiB)
+constexpr int kMetroBThreads = 1024;
+constexpr int kMetroBStage = 56 * 1024;  // floats staged per CTA (224 KiB)
 
 __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchParams bp) {
     extern __shared__ float wsm[];
     __shared__ int f_sm;
+    __shared__ float red[kMetroBThreads / 32];
     const int tid = threadIdx.x;
     const int n_items = (int)ld_relaxed_u32(bp.ctl + CTL_ITEMS);
     for (;;) {
@@ -139,19 +218,19 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
         }
         const float* lw = bp.lw + off0;
         const bool staged = Pf <= kMetroBStage;
-        if (staged) {
-            for (int64_t i = tid; i < Pf; i += kMetroBThreads) wsm[i] = __ldg(lw + i);
-            __syncthreads();
-        }
+        if (staged) stage_weights<kMetroBThreads>(lw, Pf, wsm, red, bp.ctl);
         const uint64_t seed = bp.seeds[f];
         const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
         const uint32_t Pu = (uint32_t)Pf;
         for (int64_t i = tid; i < Pf; i += kMetroBThreads) {
-            float lk = staged ? wsm[i] : __ldg(lw + i);
-            if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
             uint32_t k = (uint32_t)i;
-            if (staged) run_chain<true>(lw, wsm, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k, lk);
-            else run_chain<false>(lw, wsm, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k, lk);
+            if (staged) {
+                run_chain_w(lw, wsm, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k);
+            } else {
+                float lk = __ldg(lw + i);
+                if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
+                run_chain(lw, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k, lk);
+            }
             bp.anc[off0 + i] = (int32_t)k;
         }
         __syncthreads();  // the staging buffer is reused by the next filter

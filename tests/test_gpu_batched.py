@@ -26,7 +26,8 @@ def run_batched(kind, lw, off, seeds, B=0):
 
 def ragged_layout(seed=0):
     off, sf = workloads.batched_layout(F=40, seed=seed)
-    sizes = list(np.diff(off)) + [0, 1, 2, 3, 5, 4096, 8189, 8190, 8192, 8193, 16384 + 7, 131069 - 8]
+    # 57344 / 57345: the largest filter the batched Metropolis stages in shared memory, and one more
+    sizes = list(np.diff(off)) + [0, 1, 2, 3, 5, 4096, 8189, 8190, 8192, 8193, 16384 + 7, 57344, 57345, 131069 - 8]
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     sf = np.concatenate([sf, np.full(len(sizes) - sf.size, 1.3)])
     return off, sf
