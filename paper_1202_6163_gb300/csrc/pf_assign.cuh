@@ -420,6 +420,95 @@ __device__ __forceinline__ int window_below(const float* w, int n, float xh, flo
     return below;
 }
 
+// As window_below, and zmask gets bit i set when entry i carries the zero-weight
+// flag (sign bit), so the caller need not read the chosen entry again.
+__device__ __forceinline__ int window_below_z(const float* w, int n, float xh, float xl, uint32_t& zmask) {
+    int below = 0;
+    uint32_t z = 0;
+    if (n == 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t4 = __ldcg(reinterpret_cast<const float4*>(w) + q);
+            below += (__fsub_rn(fabsf(t4.x), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.y), xh) > xl ? 0 : 1) +
+                     (__fsub_rn(fabsf(t4.z), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.w), xh) > xl ? 0 : 1);
+            z |= ((__float_as_uint(t4.x) >> 31) | ((__float_as_uint(t4.y) >> 31) << 1) |
+                  ((__float_as_uint(t4.z) >> 31) << 2) | ((__float_as_uint(t4.w) >> 31) << 3))
+                 << (4 * q);
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            const float t = __ldcg(w + i);
+            below += __fsub_rn(fabsf(t), xh) > xl ? 0 : 1;
+            z |= (__float_as_uint(t) >> 31) << i;
+        }
+    }
+    zmask = z;
+    return below;
+}
+
+// Tile lookup of the single-launch multinomial draws: lut[k], k = 0..kLut, is
+// the last tile t whose boundary B_t is at or below the target (k / kLut) W
+// under the draws' own comparison.  A draw whose uniform lies in
+// (k / kLut, (k+1) / kLut) then lies in tiles lut[k]..lut[k+1], which narrows
+// the search over the table to a tile or two.
+constexpr int kLutBits = 12;
+constexpr int kLut = 1 << kLutBits;
+
+// The draws' comparison: is tile e's boundary at or below the target (th, tl)?
+__device__ __forceinline__ bool boundary_at_or_below(const TableEntry& e, float th, float tl) {
+    return __fadd_rn(__fsub_rn(e.bhi, th), __fsub_rn(e.blo, tl)) <= 0.f;
+}
+
+// Target u W of a uniform given as an exact pair (uh, ul), W = (Wh, Wl).
+__device__ __forceinline__ void draw_target(float uh, float ul, float Wh, float Wl, float& th, float& tl) {
+    th = __fmul_rn(uh, Wh);
+    tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
+}
+
+// Block-wide (kThreads): fills lut[0..kLut] from table[0..T); red: kWarps ints.
+__device__ inline void build_tile_lut(const TableEntry* table, int T, float Wh, float Wl, int* lut, int* red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = tid; k <= kLut; k += kThreads) lut[k] = 0;
+    __syncthreads();
+    // each tile t >= 1 marks the first lookup point whose target reaches B_t
+    for (int t = 1 + tid; t < T; t += kThreads) {
+        const TableEntry e = table[t];
+        auto reaches = [&](int k) {
+            float th, tl;
+            draw_target((float)k * (1.f / kLut), 0.f, Wh, Wl, th, tl);
+            return boundary_at_or_below(e, th, tl);
+        };
+        int k = (int)fminf(fmaxf(ceilf(e.bhi / Wh * (float)kLut), 0.f), (float)kLut);
+        while (k > 0 && reaches(k - 1)) --k;
+        while (k <= kLut && !reaches(k)) ++k;
+        if (k <= kLut) atomicMax(&lut[k], t);
+    }
+    __syncthreads();
+    // running maximum over lut[0..kLut): kLut / kThreads consecutive entries per thread
+    constexpr int per = kLut / kThreads;
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < per; ++i) m = max(m, lut[tid * per + i]);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int h = __shfl_up_sync(0xffffffffu, m, o);
+        if (lane >= o) m = max(m, h);
+    }
+    if (lane == 31) red[warp] = m;
+    int prev = __shfl_up_sync(0xffffffffu, m, 1);
+    if (lane == 0) prev = 0;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) prev = max(prev, red[w]);
+    int run = prev;
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+        run = max(run, lut[tid * per + i]);
+        lut[tid * per + i] = run;
+    }
+    if (tid == kThreads - 1) lut[kLut] = max(lut[kLut], run);
+    __syncthreads();
+}
+
 // Single-launch multinomial draw over three levels of the tiles' cumulative
 // weights: every 2^c1shift-th |v| of each tile (c1, shared memory, c1shift >=
 // 8), every 16th (c2, global, cpt2 per tile, each tile's block 64-byte
@@ -429,21 +518,29 @@ __device__ __forceinline__ int window_below(const float* w, int n, float xh, flo
 // 16-entry window whole.  The predicate and the monotone sequence are those of
 // the plain search, so the result is the same, with two dependent 64-byte
 // reads per draw (plus c1shift - 8 small ones) instead of a dozen 4-byte ones.
-__device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const TableEntry* table, int T, const float* v,
-                                                           const float* c2, int cpt2, const float* c1, int cpt1,
-                                                           int c1shift, int tile, int64_t PA, int lead, float Wh,
-                                                           float Wl) {
-    float uh, ul;
-    u32_pair(x, uh, ul);
-    const float th = __fmul_rn(uh, Wh);
-    const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
-    int lo = 0, hi = T - 1;
+__device__ __forceinline__ int last_tile_at_or_below(const TableEntry* table, int lo, int hi, float th, float tl) {
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const float d = __fadd_rn(__fsub_rn(table[mid].bhi, th), __fsub_rn(table[mid].blo, tl));
-        if (d <= 0.f) lo = mid;
+        if (boundary_at_or_below(table[mid], th, tl)) lo = mid;
         else hi = mid - 1;
     }
+    return lo;
+}
+
+__device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const TableEntry* table, const int* lut, int T,
+                                                           const float* v, const float* c2, int cpt2, const float* c1,
+                                                           int cpt1, int c1shift, int tile, int64_t PA, int lead,
+                                                           float Wh, float Wl) {
+    float uh, ul, th, tl;
+    u32_pair(x, uh, ul);
+    draw_target(uh, ul, Wh, Wl, th, tl);
+    // the last tile whose boundary is at or below the target: searched between
+    // the lookup points around u, then confirmed (the predicate is monotone in
+    // t, so a confirmed tile is the plain binary search's result over all T)
+    const int kq = (int)(x >> (32 - kLutBits));
+    int lo = last_tile_at_or_below(table, lut[kq], min(lut[kq + 1], T - 1), th, tl);
+    if (!boundary_at_or_below(table[lo], th, tl) || (lo + 1 < T && boundary_at_or_below(table[lo + 1], th, tl)))
+        lo = last_tile_at_or_below(table, 0, T - 1, th, tl);
     while (lo > 0 && table[lo].il < 0) --lo;
     const TableEntry e = table[lo];
     float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
@@ -490,10 +587,11 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
         m2 += window_below(c2t + m2, min(16, n2 - m2), xh, xl);
         const int w0 = m2 << 4;
         const int wn = min(16, nt - w0);
-        const int below = window_below(v + b0 + w0, wn, xh, xl);
+        uint32_t zmask;
+        const int below = window_below_z(v + b0 + w0, wn, xh, xl, zmask);
         idx = w0 + below;
         if (below >= wn) idx = e.il;  // not reached: the window's last sample is above the target
-        else if (zero_flag(__ldcg(v + b0 + idx))) {  // rounding landed on a zero weight: the next positive one
+        else if ((zmask >> below) & 1u) {  // rounding landed on a zero weight: the next positive one
             int f = e.il;
             for (int z = idx + 1; z < nt; ++z)
                 if (!zero_flag(__ldcg(v + b0 + z))) {

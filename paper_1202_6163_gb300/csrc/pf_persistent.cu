@@ -42,10 +42,13 @@ struct PersistShared {
     int ok;
 };
 // Dynamic shared memory: PersistShared, then either the staging buffer
-// int32 out[kIoCap] (systematic, stratified) or TableEntry table[T] (multinomial).
+// int32 out[kIoCap] (systematic, stratified) or, for multinomial, TableEntry
+// table[T], the tile lookup int lut[kLut + 1] and the level-1 samples
+// float c1[T * cpt1] (sized by the launch).
 
 __host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T) {
-    return sizeof(PersistShared) + (kind == KIND_MULTI ? (size_t)T * sizeof(TableEntry) : kIoCap * sizeof(int32_t));
+    return sizeof(PersistShared) + (kind == KIND_MULTI ? (size_t)T * sizeof(TableEntry) + (kLut + 1) * sizeof(int)
+                                                       : kIoCap * sizeof(int32_t));
 }
 
 // ---------------------------------------------------------------------------
@@ -156,12 +159,13 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
     const float Wh = sm.as.W_hi, Wl = sm.as.W_lo;
     const int64_t nq = (p.P + 3) >> 2;  // four draws per Philox block
     const int64_t q_beg = nq * cta / G, q_end = nq * (cta + 1) / G;
-    // the level-1 samples of every tile, after the table (published before the arrival)
-    float* c1 = reinterpret_cast<float*>(const_cast<TableEntry*>(table) + T);
+    // the tile lookup, then the level-1 samples of every tile (published before the arrival)
+    int* lut = reinterpret_cast<int*>(const_cast<TableEntry*>(table) + T);
+    float* c1 = reinterpret_cast<float*>(lut + kLut + 1);
     if (p.c2_out) {
         const int nc = T * p.cpt1;
         for (int i = tid; i < nc; i += kThreads) c1[i] = __ldcg(p.c1_out + i);
-        __syncthreads();
+        build_tile_lut(table, T, Wh, Wl, lut, sm.red_k);
     }
     for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
         const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
@@ -169,7 +173,7 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
         if (p.c2_out) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                a[s] = multinomial_draw_3level(word_of(r, s), table, T, p.v_out, p.c2_out, p.cpt2, c1, p.cpt1,
+                a[s] = multinomial_draw_3level(word_of(r, s), table, lut, T, p.v_out, p.c2_out, p.cpt2, c1, p.cpt1,
                                                p.c1shift, p.tile, p.P + p.lead, p.lead, Wh, Wl);
         } else {
             multinomial_draws4<false>(r, table, T, p.v_out, p.tile, p.P + p.lead, p.lead, Wh, Wl, a);
