@@ -66,6 +66,24 @@ def test_batched_metropolis_ragged_filters():
         assert rep.ok, (f, rep.summary())
 
 
+def test_batched_metropolis_wide_range():
+    # spreads of 40: most staged weights fall below 2^-100 and those states decide
+    # from the log-weights (filters of 3000 and 57000 are staged, 60000 is not)
+    sizes = [3000, 57000, 60000, 1]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    lw = workloads.batched_logw(off, np.full(len(sizes), 40.0), seed=6)
+    lw[np.random.default_rng(6).random(lw.size) < 0.05] = -np.inf
+    seeds = workloads.batched_seeds(len(sizes), base=90)
+    B = 20
+    a, st = run_batched(pf.PF_METROPOLIS, lw, off, seeds, B=B)
+    assert st == pf.PF_OK
+    for f in range(len(sizes)):
+        l = lw[off[f]:off[f + 1]]
+        rep = check_metropolis(l, B, a[off[f]:off[f + 1]], oracle.metropolis(l, B, int(seeds[f]), f), int(seeds[f]),
+                               filter_id=f)
+        assert rep.ok, (f, rep.summary())
+
+
 def test_batched_bad_filters_are_reported_and_others_resampled():
     sizes = [1000, 2000, 150000, 500]  # the third exceeds the per-filter limit
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)

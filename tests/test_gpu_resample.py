@@ -130,6 +130,20 @@ def test_zero_weights_never_selected():
         assert check_metropolis(lw, 16, a, oracle.metropolis(lw, 16, 1), 1).ok
 
 
+def test_metropolis_staged_weights_over_a_wide_range():
+    # log-weights N(0, 40^2): most staged weights exp(lw - max) fall below 2^-100 or
+    # underflow, so chains in those states decide from the log-weights; P = 3000 and
+    # 40000 are staged in shared memory, 60000 is read through L2
+    rng = np.random.default_rng(11)
+    for P in (3000, 40000, 60000):
+        lw = (40.0 * rng.standard_normal(P)).astype(np.float32)
+        lw[rng.random(P) < 0.05] = -np.inf
+        a, st = gpu_resample(pf.pf_resample_metropolis, lw, 4, B=24)
+        assert st == pf.PF_OK
+        rep = check_metropolis(lw, 24, a, oracle.metropolis(lw, 24, 4), 4)
+        assert rep.ok, rep.summary()
+
+
 def test_one_hot_and_equal_weights():
     for P in (1, 9, 70001):
         lw = np.full(P, -np.inf, np.float32)
