@@ -157,7 +157,8 @@ def run_gpu(args):
                "metropolis": lambda: run_metropolis_sweep(args, pf, torch, dev),
                "inplace": lambda: run_inplace(args, pf, torch, dev),
                "sweep": lambda: run_size_sweep(args, pf, torch, dev, hbm_peak),
-               "sorted": lambda: run_sorted_ablation(args, pf, torch, dev)}[args.only]()
+               "sorted": lambda: run_sorted_ablation(args, pf, torch, dev),
+               "phases": lambda: run_phases(args, pf, torch, dev, stream)}[args.only]()
         if rank == 0:
             print(json.dumps({"leg": args.only, **leg}))
         return
@@ -894,6 +895,97 @@ def cpu_baseline(args, budget_s=None):
             "s_per_step": round(per_step, 4)}
 
 
+def run_phases(args, pf, torch, dev, stream):
+    """Where the time of one call goes, from the library's phase trace
+    (pf_set_trace_buffer): for the single-launch systematic, stratified and
+    multinomial calls at P = 2^20, per CTA, the median time of each phase
+    (scan, grid-wide wait, carries, assignment or draws) and when the last CTA
+    had passed it, in us after the first CTA started, beside the CUDA-event time
+    of the call; for the batched systematic call over the 4096 filters, per work
+    item, the median phase times and how busy the CTAs were.  Medians over 20
+    calls, L2 flushed before each."""
+    import numpy as np
+
+    from paper_1202_6163_gb300 import workloads
+    W = pf.PF_TRACE_WORDS
+    cap = 1 << 14
+    buf = torch.zeros(cap * W, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    reps = 20
+
+    def traced(call):
+        out = []
+        for r in range(reps + 3):
+            buf.zero_()
+            flush.zero_()
+            torch.cuda._sleep(20000)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call(r)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            rec = buf.view(cap, W).cpu().numpy()
+            rec = rec[rec[:, 0] != 0]
+            if r >= 3:
+                out.append((e0.elapsed_time(e1) * 1e3, rec))
+        if pf.pf_get_device_status(stream) != pf.PF_OK:
+            raise RuntimeError("device status not OK in the phase trace")
+        return out
+
+    def med(x):
+        return round(float(np.median(x)), 2)
+
+    P = args.P
+    lw = torch.from_numpy(workloads.gaussian_logw(P, SPREAD, seed=SEED)).to(dev)
+    anc = torch.empty(P, dtype=torch.int32, device=dev)
+    pf.pf_set_trace_buffer(buf, cap)
+    try:
+        single = {}
+        for name, fn in (("systematic", pf.pf_resample_systematic), ("stratified", pf.pf_resample_stratified),
+                         ("multinomial", pf.pf_resample_multinomial)):
+            runs = traced(lambda r, fn=fn: fn(lw, P, 0, SEED + r, anc, stream))
+            rows = []
+            for ev, rec in runs:
+                t = (rec[:, :5] - rec[:, 0].min()) / 1e3  # us after the first CTA started
+                rows.append([ev, len(rec), t[:, 0].max(), np.median(t[:, 1] - t[:, 0]), t[:, 1].max(),
+                             np.median(t[:, 2] - t[:, 1]), t[:, 2].max(), np.median(t[:, 3] - t[:, 2]), t[:, 3].max(),
+                             np.median(t[:, 4] - t[:, 3]), t[:, 4].max()])
+            m = np.median(np.array(rows), axis=0)
+            single[name] = {"event_us": round(m[0], 2), "ctas": int(m[1]), "last_cta_start_us": round(m[2], 2),
+                            "scan_us": round(m[3], 2), "all_scanned_us": round(m[4], 2),
+                            "wait_us": round(m[5], 2), "all_released_us": round(m[6], 2),
+                            "carries_us": round(m[7], 2), "all_carried_us": round(m[8], 2),
+                            "assign_us": round(m[9], 2), "last_cta_end_us": round(m[10], 2),
+                            "outside_kernel_us": round(m[0] - m[10], 2)}
+        F = 4096
+        off, sf = workloads.batched_layout(F=F, seed=0)
+        blw = torch.from_numpy(workloads.batched_logw(off, sf, seed=0)).to(dev)
+        d_off = torch.from_numpy(off).to(dev)
+        seeds = torch.from_numpy(workloads.batched_seeds(F, base=0).view(np.int64)).to(dev)
+        banc = torch.empty(blw.numel(), dtype=torch.int32, device=dev)
+        runs = traced(lambda r: pf.pf_resample_batched(pf.PF_SYSTEMATIC, blw, d_off, F, 0, seeds, banc, stream))
+        rows = []
+        for ev, rec in runs:
+            t = (rec[:, :5] - rec[:, 0].min()) / 1e3
+            span = t[:, 4].max()
+            ctas = np.unique(rec[:, 5])
+            busy = float(np.sum(t[:, 4] - t[:, 0]))
+            split = rec[:, 7] != 31
+            rows.append([ev, len(rec), len(ctas), span, np.median(t[:, 1] - t[:, 0]),
+                         np.median((t[:, 2] - t[:, 1])[split]) if split.any() else 0.0,
+                         np.median(t[:, 3] - t[:, 2]), np.median(t[:, 4] - t[:, 3]), busy / (len(ctas) * span)])
+        m = np.median(np.array(rows), axis=0)
+        batched = {"event_us": round(m[0], 2), "items": int(m[1]), "ctas": int(m[2]), "kernel_span_us": round(m[3], 2),
+                   "item_scan_us": round(m[4], 2), "split_item_wait_us": round(m[5], 2),
+                   "item_carries_us": round(m[6], 2), "item_assign_us": round(m[7], 2),
+                   "cta_busy_fraction": round(m[8], 3)}
+    finally:
+        pf.pf_set_trace_buffer(None)
+    return {"workload": f"single filter P={P}, log-weights N(0,1); batched: 4096 filters, P_f log-uniform in "
+                        f"[256, 65536]", "reps": reps, "single": single, "batched_systematic": batched,
+            "time_base": "GPU global timer, us after the first CTA started"}
+
+
 def cpu_baseline_batched():
     """The oracle on the whole 4096-filter workload of the batched leg (every
     filter, each resampler), filters spread over all host cores by threads:
@@ -981,7 +1073,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-bootstrap", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace", "sweep", "sorted"],
+    ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace", "sweep", "sorted",
+                                       "phases"],
                     default=None,
                     help="run one secondary leg alone and print its JSON (for profiling)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

@@ -330,6 +330,34 @@ pf_status pf_set_wait_limit_ns(uint64_t ns);
 pf_status pf_debug_skip_publish(int64_t tile);
 
 /*
+ * Phase trace of the tile kernels (a diagnostic; off by default).  While a
+ * buffer is set, every later single-launch systematic, stratified or
+ * multinomial call writes one record per CTA (record index = CTA), and every
+ * batched systematic, stratified, multinomial or Metropolis call one record
+ * per work item (record index = the item's ticket, items in the order the
+ * plan pass issues them), of PF_TRACE_WORDS 64-bit words:
+ *   [0] GPU global timer (ns) when the CTA started / took the item
+ *   [1] ... when its tile scans and record publication were done
+ *   [2] ... when its wait ended: the grid-wide gather of the single-launch
+ *       kernel, the filter's other tiles for a batched filter split over
+ *       several CTAs ([2] = [1] where nothing is waited for)
+ *   [3] ... when its carries (tile boundaries) were formed
+ *   [4] ... when its ancestors were written
+ *   [5] CTA index   [6] filter (batched; 0 otherwise)
+ *   [7] tiles owned (single launch) or the item's tile code (batched)
+ * All CTAs read the same timer, so the records of one call share a time base.
+ *   buf       device memory of capacity * PF_TRACE_WORDS * 8 bytes, caller
+ *             owned and kept alive while set; NULL turns tracing off.
+ *   capacity  records; those past it are not written (>= 0).
+ * Each call writes from record 0 over what the previous one left; read buf
+ * after synchronising the call's stream.  Concurrent calls on several streams
+ * share the buffer.  Errors: PF_ERR_INVALID for capacity < 0, a misaligned
+ * buf (8 bytes), or a non-NULL buf with capacity 0.
+ */
+#define PF_TRACE_WORDS 8
+pf_status pf_set_trace_buffer(uint64_t* buf, int64_t capacity);
+
+/*
  * Diagnostic (not part of the method): the rate, in reads per second, of
  * random 4-byte reads from buf[0..n) once it is resident in L2.  This is the
  * ceiling of the Metropolis resampler when the log-weights live in L2 (one

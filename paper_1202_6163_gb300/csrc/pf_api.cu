@@ -59,6 +59,9 @@ DeviceInfo g_dev[kMaxDevices];
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 uint64_t g_wait_ns = 1000000000ull;
 int64_t g_skip_tile = -1;
+static_assert(kTraceWords == PF_TRACE_WORDS, "trace record layout");
+uint64_t* g_trace = nullptr;  // phase-trace buffer (pf_set_trace_buffer), or null
+int64_t g_trace_cap = 0;
 
 pf_status cuda_fail(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return PF_OK;
@@ -255,6 +258,8 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     p.cpt2 = cpt2;
     p.cpt1 = cpt1;
     p.c1shift = c1shift;
+    p.trace = g_trace;
+    p.trace_cap = g_trace_cap;
     return cuda_fail(launch_sorted_persistent(kind, p, G, s), "persistent launch");
 }
 
@@ -392,6 +397,8 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     bp.wait_ns = g_wait_ns;
     bp.skip_tile = kind == PF_STRATIFIED || kind == PF_SYSTEMATIC ? (int)g_skip_tile : -1;
     if (bp.skip_tile >= 0) g_skip_tile = -1;
+    bp.trace = g_trace;
+    bp.trace_cap = g_trace_cap;
     if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
     return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
 }
@@ -505,6 +512,14 @@ pf_status pf_set_wait_limit_ns(uint64_t ns) {
     if (ns == 0) return PF_ERR_INVALID;
     std::lock_guard<std::mutex> lk(g_mu);
     g_wait_ns = ns;
+    return PF_OK;
+}
+
+pf_status pf_set_trace_buffer(uint64_t* buf, int64_t capacity) {
+    if (capacity < 0 || (((uintptr_t)buf) & 7u) != 0 || (buf != nullptr && capacity == 0)) return PF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_trace = buf;
+    g_trace_cap = buf ? capacity : 0;
     return PF_OK;
 }
 

@@ -140,6 +140,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
         SortedParams p;
         filter_params(bp, f, off0, Pf, lead, Tf, p);
         int32_t* out = reinterpret_cast<int32_t*>(region);
+        if (bp.trace) {
+            trace_stamp(bp.trace, bp.trace_cap, ticket, 0);
+            for (int w = 1; w <= 4; ++w) trace_put(bp.trace, bp.trace_cap, ticket, w, 0);
+            trace_put(bp.trace, bp.trace_cap, ticket, 5, blockIdx.x);
+            trace_put(bp.trace, bp.trace_cap, ticket, 6, (uint64_t)f);
+            trace_put(bp.trace, bp.trace_cap, ticket, 7, (uint64_t)c_item);
+        }
 
         if (KIND != KIND_MULTI) {
             // ---- systematic / stratified: one tile (a one-tile filter is its own item) ----
@@ -149,6 +156,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
             uint32_t* rec = reinterpret_cast<uint32_t*>(bp.records + (ticket - c));  // the filter's Tf records
             uint32_t* arrive = bp.counters + 2 * f;
             if (tid == 0) {
+                trace_stamp(bp.trace, bp.trace_cap, ticket, 1);
                 int ok = 1;
                 if (Tf > 1 && c == bp.skip_tile) {
                     ok = 0;  // test hook: withhold this tile's record; the filter's other tiles time out
@@ -173,6 +181,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                     sm.ril[0] = ts.i_last;
                 }
                 sm.skip = !ok;
+                trace_stamp(bp.trace, bp.trace_cap, ticket, 2);
             }
             __syncthreads();
             if (!sm.skip) {
@@ -189,9 +198,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                 }
                 __syncthreads();
                 if (!sm.skip) {
+                    trace_stamp(bp.trace, bp.trace_cap, ticket, 3);
                     if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
                     __syncthreads();
                     assign_offspring<KIND>(p, sm.as, out, th, ts, t0 - lead);
+                    if (bp.trace) {
+                        __syncthreads();
+                        trace_stamp(bp.trace, bp.trace_cap, ticket, 4);
+                    }
                 }
             }
             // the last of a split filter's CTAs to leave resets its counters
@@ -228,6 +242,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
             }
             __syncthreads();
         }
+        trace_stamp(bp.trace, bp.trace_cap, ticket, 1);
+        trace_stamp(bp.trace, bp.trace_cap, ticket, 2);
         if (tid < 32) {
             const bool in = lane < Tf;
             filter_carries<KIND>(sm, bp, Tf, lane, in ? sm.rk[lane] : 0, in ? sm.rsh[lane] : 0.f,
@@ -235,6 +251,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
         }
         __syncthreads();
         if (sm.skip) continue;
+        trace_stamp(bp.trace, bp.trace_cap, ticket, 3);
 
         if (KIND == KIND_MULTI) {
             const int64_t nq = (Pf + 3) >> 2;  // four draws per Philox block
@@ -255,6 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                     if (4 * q + s < Pf) p.anc[4 * q + s] = a[s];
             }
             __syncthreads();
+            trace_stamp(bp.trace, bp.trace_cap, ticket, 4);
             continue;
         }
     }

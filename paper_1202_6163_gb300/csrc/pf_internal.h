@@ -65,6 +65,8 @@ struct SortedParams {
     float* c2_out;    // multinomial: every 16th |v| of each tile (cpt2 per tile), or null
     float* c1_out;    // multinomial: every 2^c1shift-th |v| of each tile (cpt1 per tile)
     int cpt2, cpt1, c1shift;
+    uint64_t* trace;     // phase records (kTraceWords words each), or null
+    int64_t trace_cap;   // records the trace buffer holds
 };
 
 // Batched call: F filters, filter f owns lw[offsets[f] .. offsets[f+1]).
@@ -83,7 +85,26 @@ struct BatchParams {
     uint32_t* counters;       // two per filter (arrivals, departures), zero between launches
     uint64_t wait_ns;         // limit of the wait for a split filter's records
     int skip_tile;            // test hook: tile skip_tile of every split filter withholds its record (-1: off)
+    uint64_t* trace;     // phase records per work item (kTraceWords words each), or null
+    int64_t trace_cap;
 };
+
+// Phase record of a traced CTA or work item: global-timer stamps at the start,
+// after the scans, after the wait, after the carries and at the end, then the
+// CTA, the filter and a tile code.
+constexpr int kTraceWords = 8;
+
+// Thread 0 writes word w of record i (a global-timer stamp, or `value`).
+__device__ __forceinline__ void trace_put(uint64_t* trace, int64_t cap, int64_t i, int w, uint64_t value) {
+    if (trace != nullptr && threadIdx.x == 0 && i < cap) trace[i * kTraceWords + w] = value;
+}
+__device__ __forceinline__ void trace_stamp(uint64_t* trace, int64_t cap, int64_t i, int w) {
+    if (trace != nullptr && threadIdx.x == 0 && i < cap) {
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        trace[i * kTraceWords + w] = t;
+    }
+}
 
 // One step of F bootstrap filters on the linear-Gaussian test model.
 struct LgParams {

@@ -218,7 +218,14 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
         }
         const float* lw = bp.lw + off0;
         const bool staged = Pf <= kMetroBStage;
+        if (bp.trace) {
+            trace_stamp(bp.trace, bp.trace_cap, ticket, 0);
+            trace_put(bp.trace, bp.trace_cap, ticket, 5, blockIdx.x);
+            trace_put(bp.trace, bp.trace_cap, ticket, 6, (uint64_t)f);
+            trace_put(bp.trace, bp.trace_cap, ticket, 7, (uint64_t)(bp.items[ticket] & 31));
+        }
         if (staged) stage_weights<kMetroBThreads>(lw, Pf, wsm, red, bp.ctl);
+        for (int w = 1; w <= 3; ++w) trace_stamp(bp.trace, bp.trace_cap, ticket, w);
         const uint64_t seed = bp.seeds[f];
         const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
         const uint32_t Pu = (uint32_t)Pf;
@@ -234,6 +241,7 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
             bp.anc[off0 + i] = (int32_t)k;
         }
         __syncthreads();  // the staging buffer is reused by the next filter
+        trace_stamp(bp.trace, bp.trace_cap, ticket, 4);
     }
     if (tid == 0) {
         __threadfence();

@@ -201,6 +201,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     const int t_first = blockIdx.x * R;
     const int t_count = max(0, min(R, p.n_tiles - t_first));
     uint32_t* rec = reinterpret_cast<uint32_t*>(p.slots);
+    if (p.trace) {
+        trace_put(p.trace, p.trace_cap, blockIdx.x, 0, t_start);
+        for (int w = 1; w <= 4; ++w) trace_put(p.trace, p.trace_cap, blockIdx.x, w, 0);
+        trace_put(p.trace, p.trace_cap, blockIdx.x, 5, blockIdx.x);
+        trace_put(p.trace, p.trace_cap, blockIdx.x, 6, 0);
+        trace_put(p.trace, p.trace_cap, blockIdx.x, 7, (uint64_t)t_count);
+    }
 
     // pass 1: scan and record every owned tile
     TileThread th;
@@ -229,9 +236,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         __syncthreads();
     }
 
+    trace_stamp(p.trace, p.trace_cap, blockIdx.x, 1);
     bool ok = arrive_and_wait(p, sm, skip, epoch, t_start);
+    trace_stamp(p.trace, p.trace_cap, blockIdx.x, 2);
     if (!ok && tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
     if (ok) ok = carries<KIND>(p, sm, reinterpret_cast<TableEntry*>(region), t_first, t_count);
+    if (ok) trace_stamp(p.trace, p.trace_cap, blockIdx.x, 3);
     // every CTA read the epoch before arriving, and CTA 0 has seen all arrivals
     // (or waited out its limit): reset the counter the next launch will use and
     // advance the epoch
@@ -243,6 +253,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
 
     if (KIND == KIND_MULTI) {
         multinomial_draws(p, sm, reinterpret_cast<const TableEntry*>(region));
+        if (p.trace) {
+            __syncthreads();
+            trace_stamp(p.trace, p.trace_cap, blockIdx.x, 4);
+        }
         return;
     }
     // pass 2: offsets of every owned tile (the last tile's scan is still in registers)
@@ -255,6 +269,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], ts.k);
         __syncthreads();
         assign_offspring<KIND, KK>(p, sm.as, out, th, ts, t0 - p.lead);
+    }
+    if (p.trace) {
+        __syncthreads();
+        trace_stamp(p.trace, p.trace_cap, blockIdx.x, 4);
     }
 }
 

@@ -40,6 +40,7 @@ SIGNATURES = {
     "pf_metropolis_bias": (ctypes.c_double, [_I64, ctypes.c_double, _I64]),
     "pf_set_wait_limit_ns": (_INT, [_U64]),
     "pf_debug_skip_publish": (_INT, [_I64]),
+    "pf_set_trace_buffer": (_INT, [_VP, _I64]),
     "pf_version": (_INT, []),
     "pf_resample_multinomial_static": (_INT, [_VP, _I64, _U64, _VP, _VP, _VP]),
     "pf_probe_l2_random_reads": (_INT, [_VP, _I64, _INT, ctypes.POINTER(ctypes.c_double)]),
@@ -209,6 +210,15 @@ def pf_set_wait_limit_ns(ns: int):
 
 def pf_debug_skip_publish(tile: int):
     _check(load().pf_debug_skip_publish(tile), "pf_debug_skip_publish")
+
+
+PF_TRACE_WORDS = 8
+
+
+def pf_set_trace_buffer(buf, capacity: int = 0):
+    """Phase trace of the tile kernels into buf (device, capacity x PF_TRACE_WORDS
+    64-bit words); None turns tracing off."""
+    _check(load().pf_set_trace_buffer(_ptr(buf), capacity if buf is not None else 0), "pf_set_trace_buffer")
 
 
 def pf_resample_multinomial_static(logw, P, seed, ancestors, device_status=None, stream=None):
