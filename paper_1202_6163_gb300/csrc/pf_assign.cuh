@@ -79,30 +79,45 @@ __device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i,
     sm.inv_rho = PW.hi * pow2f(k_tile - sm.K);
 }
 
+// Run-length decode staging: two buffers of kIoCap entries, used by
+// successive chunks in turn.  A chunk's entries are tagged with the chunk's
+// epoch, (epoch << kLocalBits) | element, so entries left by earlier chunks
+// are smaller than all of its own and no clearing pass is needed; alternating
+// the buffers lets a chunk start before every thread has stored the previous
+// one.  stage_init fills both buffers with -1 (below every tag) and must run
+// once per launch before the first chunk.
+constexpr int kLocalBits = 13;  // tile-local element index
+static_assert(kTileMax <= (1 << kLocalBits), "element index must fit the tag's low bits");
+constexpr uint32_t kEpochMax = (1u << (31 - kLocalBits)) - 1;  // tags stay positive as int32
+
+__device__ __forceinline__ void stage_init(int32_t* stage) {  // stage: 16-byte aligned
+    for (int i = threadIdx.x; i < 2 * kIoCap / 4; i += kThreads)
+        reinterpret_cast<int4*>(stage)[i] = make_int4(-1, -1, -1, -1);
+}
+
 // One chunk [c0, c1) of the tile's offsets: each positive element marks the
-// first slot of its run [N_{i-1}, N_i) with its index (runs of later elements
-// start later, so indices increase along the chunk), the element whose run
-// covers the chunk's first slot marks that slot, and an inclusive max-scan
-// over the chunk fills every run.  Chunk slot s sits at out[s + shift] so that
-// out[x] maps to the 16-byte aligned global position gb + x; each thread scans
-// and stores S consecutive entries (S * kThreads >= c1 - c0 + shift).
+// first slot of its run [N_{i-1}, N_i) with its tagged tile-local index (runs
+// of later elements start later, so tags increase along the chunk), the
+// element whose run covers the chunk's first slot marks that slot, and an
+// inclusive max-scan over the chunk fills every run.  Chunk slot s sits at
+// out[s + shift] so that out[x] maps to the 16-byte aligned global position
+// gb + x; each thread scans and stores S consecutive entries
+// (S * kThreads >= c1 - c0 + shift).  Ancestor = tile_base + element.
 template <int S, int KK = 0>  // KK: elements per thread when fixed, 0 = th.K
 __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared& sm, int32_t* out,
                                              const TileThread& th, long long jlo, int c0, int c1, int shift,
-                                             int start0, int32_t base) {
+                                             int start0, int32_t tile_base, int32_t tag) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0i = tid * S;
-#pragma unroll
-    for (int q = 0; q < S / 4; ++q) *reinterpret_cast<int4*>(&out[x0i + 4 * q]) = make_int4(-1, -1, -1, -1);
-    __syncthreads();
+    const int32_t mark0 = tag | th.e0;
     int a = start0;
 #pragma unroll
     for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
         if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
             const int b = __float_as_int(th.v[i]);
             if (b > a) {
-                if (a >= c0 && a < c1) out[a - c0 + shift] = base + i;
-                else if (a < c0 && b > c0) out[shift] = base + i;
+                if (a >= c0 && a < c1) out[a - c0 + shift] = mark0 + i;
+                else if (a < c0 && b > c0) out[shift] = mark0 + i;
             }
             a = b;
         }
@@ -129,31 +144,38 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
     if (lane == 31) sm.red_n[warp] = mm;
     __syncthreads();
     for (int w = 0; w < warp; ++w) carry = max(carry, sm.red_n[w]);
-    // entries x in [x0i, x0i + S) hold chunk slots x - shift
+    // entries x in [x0i, x0i + S) hold chunk slots x - shift; every slot of
+    // the chunk carries this chunk's tag (its first slot is marked)
+    constexpr int32_t kLocalMask = (1 << kLocalBits) - 1;
     const int lo = max(x0i, shift), hi = min(x0i + S, shift + (c1 - c0));
     if (hi > lo) {
         int32_t* g = p.anc + (jlo + c0 - shift) + x0i;  // 16-byte aligned
         if (lo == x0i && hi == x0i + S) {
 #pragma unroll
             for (int q = 0; q < S / 4; ++q)
-                *reinterpret_cast<int4*>(g + 4 * q) = make_int4(max(carry, r[q].x), max(carry, r[q].y),
-                                                                 max(carry, r[q].z), max(carry, r[q].w));
+                *reinterpret_cast<int4*>(g + 4 * q) = make_int4(
+                    tile_base + (max(carry, r[q].x) & kLocalMask), tile_base + (max(carry, r[q].y) & kLocalMask),
+                    tile_base + (max(carry, r[q].z) & kLocalMask), tile_base + (max(carry, r[q].w) & kLocalMask));
         } else {
 #pragma unroll
             for (int q = 0; q < S / 4; ++q) {
                 const int v4[4] = {max(carry, r[q].x), max(carry, r[q].y), max(carry, r[q].z), max(carry, r[q].w)};
 #pragma unroll
                 for (int z = 0; z < 4; ++z)
-                    if (x0i + 4 * q + z >= lo && x0i + 4 * q + z < hi) g[4 * q + z] = v4[z];
+                    if (x0i + 4 * q + z >= lo && x0i + 4 * q + z < hi) g[4 * q + z] = tile_base + (v4[z] & kLocalMask);
             }
         }
     }
-    __syncthreads();
+    // no trailing barrier: the next chunk marks the other buffer, and it reuses
+    // sm.red_n only after its own mark barrier, which every thread reaches after
+    // finishing this chunk's reads of sm.red_n
 }
 
+// stage: the two staging buffers (2 * kIoCap entries, stage_init'ed once per
+// launch); epoch: the chunk counter of the launch, identical in every thread.
 template <int KIND, int KK = 0>  // KK: elements per thread when fixed, 0 = th.K
-__device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_t* out, TileThread& th,
-                                 const TileSummary& ts, int64_t index0) {
+__device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_t* stage, uint32_t& epoch,
+                                 TileThread& th, const TileSummary& ts, int64_t index0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int noff = sm.noff;
     const long long jlo = sm.jlo;
@@ -207,21 +229,29 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
     __syncthreads();
     for (int w = 0; w < warp; ++w) prev = max(prev, sm.red_n[w]);
     const int start0 = max(prev, 0);
-    const int32_t base = (int32_t)(index0 + th.e0);  // particle index of this thread's first element
+    const int32_t tile_base = (int32_t)index0;  // particle index of the tile's element 0
 
     // Run-length decode, one staging chunk at a time (decode_chunk); chunks
     // of at most 2044 / 4092 offsets use 4 / 8 staging entries per thread.
     constexpr int kChunk = kIoCap - 4;  // offsets per chunk (room for the shift)
     for (int c0 = 0; c0 < noff; c0 += kChunk) {
+        if (++epoch > kEpochMax) {  // tags exhausted (uniform): clear both buffers and restart
+            __syncthreads();
+            stage_init(stage);
+            __syncthreads();
+            epoch = 1;
+        }
+        int32_t* out = stage + (epoch & 1u) * kIoCap;
+        const int32_t tag = (int32_t)(epoch << kLocalBits);
         const int c1 = min(noff, c0 + kChunk);
         const int shift = (int)(((uintptr_t)(p.anc + jlo + c0) >> 2) & 3u);  // to a 16-byte boundary
         const int need = c1 - c0 + shift;
         if (need <= 4 * kThreads)
-            decode_chunk<4, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+            decode_chunk<4, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
         else if (need <= 8 * kThreads)
-            decode_chunk<8, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+            decode_chunk<8, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
         else
-            decode_chunk<16, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, base);
+            decode_chunk<16, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
     }
 }
 

@@ -46,11 +46,14 @@ struct BatchShared {
     TableEntry table[kMaxOwnB];
     int f, skip;
 };
-// Dynamic shared memory after BatchShared: the staging buffer int32 out[kIoCap]
-// (systematic, stratified) or the cumulative weights float v[kTileMax] of a
-// one-tile filter (multinomial).
-
-__host__ __device__ constexpr size_t batched_smem_bytes() { return sizeof(BatchShared) + kIoCap * sizeof(int32_t); }
+// Dynamic shared memory: BatchShared, then the region -- the two run-length
+// staging buffers int32 stage[2 * kIoCap] (systematic, stratified), or the
+// cumulative weights float v[kTileMax] of a one-tile filter / the coarse
+// samples of a several-tile one (multinomial).
+__host__ __device__ constexpr size_t batched_smem_bytes() {
+    return sizeof(BatchShared) + 2 * kIoCap * sizeof(int32_t);
+}
+static_assert(sizeof(BatchShared) % 16 == 0, "the region is 16-byte aligned");
 
 
 // The filter's geometry and parameters for the tile routines.
@@ -124,6 +127,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int n_items = (int)ld_relaxed_u32(bp.ctl + CTL_ITEMS);
     TileThread th;
+    uint32_t chunks = 0;  // staging chunks decoded by this CTA
+    if (KIND != KIND_MULTI) stage_init(reinterpret_cast<int32_t*>(region));  // before the first ticket's barriers
     for (;;) {
         if (tid == 0) sm.f = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
         __syncthreads();
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
         const int Tf = (int)((PA + kTileMax - 1) / kTileMax);
         SortedParams p;
         filter_params(bp, f, off0, Pf, lead, Tf, p);
-        int32_t* out = reinterpret_cast<int32_t*>(region);
+        int32_t* stage = reinterpret_cast<int32_t*>(region);
         if (bp.trace) {
             trace_stamp(bp.trace, bp.trace_cap, ticket, 0);
             for (int w = 1; w <= 4; ++w) trace_put(bp.trace, bp.trace_cap, ticket, w, 0);
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                     trace_stamp(bp.trace, bp.trace_cap, ticket, 3);
                     if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
                     __syncthreads();
-                    assign_offspring<KIND>(p, sm.as, out, th, ts, t0 - lead);
+                    assign_offspring<KIND>(p, sm.as, stage, chunks, th, ts, t0 - lead);
                     if (bp.trace) {
                         __syncthreads();
                         trace_stamp(bp.trace, bp.trace_cap, ticket, 4);

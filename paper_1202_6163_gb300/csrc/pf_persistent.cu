@@ -41,14 +41,14 @@ struct PersistShared {
     int red_k[kWarps];
     int ok;
 };
-// Dynamic shared memory: PersistShared, then either the staging buffer
-// int32 out[kIoCap] (systematic, stratified) or, for multinomial, TableEntry
+// Dynamic shared memory: PersistShared, then either the two staging buffers
+// int32 stage[2 * kIoCap] (systematic, stratified) or, for multinomial, TableEntry
 // table[T], the tile lookup int lut[kLut + 1] and the level-1 samples
 // float c1[T * cpt1] (sized by the launch).
 
 __host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T) {
     return sizeof(PersistShared) + (kind == KIND_MULTI ? (size_t)T * sizeof(TableEntry) + (kLut + 1) * sizeof(int)
-                                                       : kIoCap * sizeof(int32_t));
+                                                       : 2 * kIoCap * sizeof(int32_t));
 }
 
 // ---------------------------------------------------------------------------
@@ -209,6 +209,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         trace_put(p.trace, p.trace_cap, blockIdx.x, 7, (uint64_t)t_count);
     }
 
+    static_assert(sizeof(PersistShared) % 16 == 0, "the staging buffers are 16-byte aligned");
+    if (KIND != KIND_MULTI) stage_init(reinterpret_cast<int32_t*>(region));  // before pass 2's barriers
+
     // pass 1: scan and record every owned tile
     TileThread th;
     TileSummary ts;
@@ -260,7 +263,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         return;
     }
     // pass 2: offsets of every owned tile (the last tile's scan is still in registers)
-    int32_t* out = reinterpret_cast<int32_t*>(region);
+    int32_t* stage = reinterpret_cast<int32_t*>(region);
+    uint32_t chunks = 0;  // staging chunks decoded by this CTA
     for (int r = t_count - 1; r >= 0; --r) {
         const int t = t_first + r;
         const int64_t t0 = (int64_t)t * p.tile;
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
             ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, (int)min((int64_t)p.tile, PA - t0), sm.tile, th);
         if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], ts.k);
         __syncthreads();
-        assign_offspring<KIND, KK>(p, sm.as, out, th, ts, t0 - p.lead);
+        assign_offspring<KIND, KK>(p, sm.as, stage, chunks, th, ts, t0 - p.lead);
     }
     if (p.trace) {
         __syncthreads();
