@@ -476,6 +476,62 @@ __device__ __forceinline__ int window_below_z(const float* w, int n, float xh, f
     return below;
 }
 
+// Quad-cooperative window count.  Every lane of the warp calls it at the same
+// point (the shuffles span the full warp).  Each lane brings a window of n <= 16
+// monotone entries at w (16-byte aligned; n = 0: none) and its target
+// (xh, xl); the four lanes of each aligned quad read each other's windows, one
+// 16-byte piece per lane, so one load instruction touches the lines of 8
+// windows instead of 32 scattered pieces.  Returns the count of this lane's
+// window entries at or below its target and, in zmask, the window's
+// zero-weight flags (sign bits, bit i for entry i).
+__device__ __forceinline__ int quad_window_below(const float* w, int n, float xh, float xl, uint32_t& zmask) {
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    // all four pieces are requested before any is used, so their latencies overlap
+    float t[4][4];
+    int nr[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int src = (lane & ~3) | r;
+        const float* wr = reinterpret_cast<const float*>(
+            __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(w), src));
+        nr[r] = __shfl_sync(0xffffffffu, n, src);
+        if (4 * q + 3 < nr[r]) {
+            const float4 t4 = __ldcg(reinterpret_cast<const float4*>(wr + 4 * q));
+            t[r][0] = t4.x;
+            t[r][1] = t4.y;
+            t[r][2] = t4.z;
+            t[r][3] = t4.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) t[r][i] = 4 * q + i < nr[r] ? __ldcg(wr + 4 * q + i) : INFINITY;
+        }
+    }
+    int mine = 0;
+    uint32_t zmine = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int src = (lane & ~3) | r;
+        const float hr = __shfl_sync(0xffffffffu, xh, src), lr = __shfl_sync(0xffffffffu, xl, src);
+        int cnt = 0;
+        uint32_t z = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            cnt += __fsub_rn(fabsf(t[r][i]), hr) > lr ? 0 : 1;  // +inf padding counts as above
+            z |= (__float_as_uint(t[r][i]) >> 31) << (4 * q + i);
+        }
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, 1);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, 2);
+        z |= __shfl_xor_sync(0xffffffffu, z, 1);
+        z |= __shfl_xor_sync(0xffffffffu, z, 2);
+        if (q == r) {
+            mine = cnt;
+            zmine = z;
+        }
+    }
+    zmask = zmine;
+    return mine;
+}
+
 // Tile lookup of the single-launch multinomial draws: lut[k], k = 0..kLut, is
 // the last tile t whose boundary B_t is at or below the target (k / kLut) W
 // under the draws' own comparison.  A draw whose uniform lies in
@@ -594,31 +650,34 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
             cn -= half + 1;
         }
     }
-    int idx = e.il;
-    if (cl < n1) {
-        const float* c2t = c2 + (int64_t)lo * cpt2;
-        int m2 = cl << (c1shift - 4);  // first c2 sample of the window
-        if (c1shift > 8) {
-            // several 16-sample blocks: the first whose last sample is above the target
-            int bl = 0, bn = min(1 << (c1shift - 8), (n2 - m2 + 15) >> 4);
-            while (bn > 0) {
-                const int half = bn >> 1;
-                const int last = min(m2 + ((bl + half + 1) << 4), n2) - 1;
-                if (__fsub_rn(__ldcg(c2t + last), xh) > xl) {
-                    bn = half;
-                } else {
-                    bl += half + 1;
-                    bn -= half + 1;
-                }
+    // levels 2 and 3 read their 16-entry windows quad-cooperatively, so every
+    // lane of the warp takes this path (n = 0 where no window is read)
+    const bool has = cl < n1;
+    const float* c2t = c2 + (int64_t)lo * cpt2;
+    int m2 = cl << (c1shift - 4);  // first c2 sample of the window
+    if (has && c1shift > 8) {
+        // several 16-sample blocks: the first whose last sample is above the target
+        int bl = 0, bn = min(1 << (c1shift - 8), (n2 - m2 + 15) >> 4);
+        while (bn > 0) {
+            const int half = bn >> 1;
+            const int last = min(m2 + ((bl + half + 1) << 4), n2) - 1;
+            if (__fsub_rn(__ldcg(c2t + last), xh) > xl) {
+                bn = half;
+            } else {
+                bl += half + 1;
+                bn -= half + 1;
             }
-            m2 += bl << 4;
         }
-        // level 2: the block of 16 samples, then level 3: the 16 elements
-        m2 += window_below(c2t + m2, min(16, n2 - m2), xh, xl);
-        const int w0 = m2 << 4;
-        const int wn = min(16, nt - w0);
-        uint32_t zmask;
-        const int below = window_below_z(v + b0 + w0, wn, xh, xl, zmask);
+        m2 += bl << 4;
+    }
+    // level 2: the block of 16 samples, then level 3: the 16 elements
+    uint32_t zmask;
+    m2 += quad_window_below(c2t + m2, has ? min(16, n2 - m2) : 0, xh, xl, zmask);
+    const int w0 = m2 << 4;
+    const int wn = has ? min(16, nt - w0) : 0;
+    const int below = quad_window_below(v + b0 + w0, wn, xh, xl, zmask);
+    int idx = e.il;
+    if (has) {
         idx = w0 + below;
         if (below >= wn) idx = e.il;  // not reached: the window's last sample is above the target
         else if ((zmask >> below) & 1u) {  // rounding landed on a zero weight: the next positive one

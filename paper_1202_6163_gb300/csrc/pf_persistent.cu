@@ -167,7 +167,12 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
         for (int i = tid; i < nc; i += kThreads) c1[i] = __ldcg(p.c1_out + i);
         build_tile_lut(table, T, Wh, Wl, lut, sm.red_k);
     }
-    for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
+    // the loop runs the same number of times in every thread: the three-level
+    // draws read their windows quad-cooperatively across the warp
+    for (int64_t q0 = q_beg; q0 < q_end; q0 += kThreads) {
+        const int64_t q = q0 + tid < q_end ? q0 + tid : q_beg;  // a lane past the end redraws block q_beg
+        const bool mine = q0 + tid < q_end;
+        if (!__any_sync(0xffffffffu, mine)) continue;  // the whole warp is past the end
         const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
         int32_t a[4];
         if (p.c2_out) {
@@ -179,6 +184,7 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
             multinomial_draws4<false>(r, table, T, p.v_out, p.tile, p.P + p.lead, p.lead, Wh, Wl, a);
         }
         const int64_t j = 4 * q;
+        if (!mine) continue;
         if (j + 3 < p.P && (((uintptr_t)(p.anc + j)) & 15u) == 0) {
             *reinterpret_cast<int4*>(p.anc + j) = make_int4(a[0], a[1], a[2], a[3]);
         } else {
