@@ -342,140 +342,6 @@ __device__ __forceinline__ void multinomial_draws4(const u32x4& r, const TableEn
     }
 }
 
-// One multinomial draw of a filter whose tiles' cumulative weights v are in
-// global memory (L2) and whose every 16th |v| (and each tile's last one) is
-// in shared memory: tile search in the table, then a search in the tile's
-// coarse samples for the first window of 16 elements whose last sample exceeds
-// the tile-local target, then that window read whole (64 bytes, 16-byte
-// aligned) and the first element above the target counted in registers.
-// Same predicate on the same monotone sequence as the plain search, so the
-// same result; one 64-byte read from L2 per draw instead of a dozen.
-constexpr int kWinShift = 4;
-constexpr int kWin = 1 << kWinShift;
-__device__ __forceinline__ int32_t multinomial_draw_windowed(uint32_t x, const TableEntry* table, int T,
-                                                             const float* v, const float* coarse, int cpt, int tile,
-                                                             int64_t PA, int lead, float Wh, float Wl) {
-    float uh, ul;
-    u32_pair(x, uh, ul);
-    const float th = __fmul_rn(uh, Wh);
-    const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
-    int lo = 0, hi = T - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        const float d = __fadd_rn(__fsub_rn(table[mid].bhi, th), __fsub_rn(table[mid].blo, tl));
-        if (d <= 0.f) lo = mid;
-        else hi = mid - 1;
-    }
-    while (lo > 0 && table[lo].il < 0) --lo;
-    const TableEntry e = table[lo];
-    float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
-    float xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
-    if (xh + xl < 0.f) {
-        xh = 0.f;
-        xl = 0.f;
-    }
-    const int64_t b0 = (int64_t)lo * tile;
-    const int nt = (int)min((int64_t)tile, PA - b0);
-    // coarse: first window whose last sample is above the target
-    const float* c = coarse + lo * cpt;
-    int cl = 0, cn = (nt + kWin - 1) >> kWinShift;
-    while (cn > 0) {
-        const int half = cn >> 1;
-        if (__fsub_rn(c[cl + half], xh) > xl) {
-            cn = half;
-        } else {
-            cl += half + 1;
-            cn -= half + 1;
-        }
-    }
-    int idx = e.il;
-    const int w0 = cl << kWinShift;
-    if (w0 < nt) {
-        const float* vt = v + b0 + w0;
-        const int wn = min(kWin, nt - w0);
-        int below = 0;  // elements of the window at or below the target
-        float last = 0.f;
-        if (wn == kWin) {
-#pragma unroll
-            for (int q = 0; q < kWin / 4; ++q) {
-                const float4 t4 = __ldcg(reinterpret_cast<const float4*>(vt) + q);
-                below += (__fsub_rn(fabsf(t4.x), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.y), xh) > xl ? 0 : 1) +
-                         (__fsub_rn(fabsf(t4.z), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.w), xh) > xl ? 0 : 1);
-            }
-        } else {
-            for (int i = 0; i < wn; ++i) below += __fsub_rn(fabsf(__ldcg(vt + i)), xh) > xl ? 0 : 1;
-        }
-        (void)last;
-        if (below < wn) {
-            idx = w0 + below;
-            if (zero_flag(__ldcg(v + b0 + idx))) {  // rounding landed on a zero weight: the next positive one
-                int f = e.il;
-                for (int z = idx + 1; z < nt; ++z)
-                    if (!zero_flag(__ldcg(v + b0 + z))) {
-                        f = z;
-                        break;
-                    }
-                idx = f;
-            }
-        }
-    }
-    return (int32_t)(b0 + idx - lead);
-}
-
-// Every 16th |v| of a tile (and its last one), from this thread's elements,
-// into the tile's coarse samples (shared memory).
-__device__ __forceinline__ void write_tile_coarse(const TileThread& th, int n, float* c) {
-#pragma unroll
-    for (int i = 0; i < kMaxPerThread; ++i) {
-        const int e = th.e0 + i;
-        if (i < th.K && e < n && (((e + 1) & (kWin - 1)) == 0 || e == n - 1)) c[e >> kWinShift] = fabsf(th.v[i]);
-    }
-}
-
-// Count of the first n (<= 16) entries of a 16-aligned window of |values|
-// at or below the tile-local target (xh, xl); the window is monotone, so the
-// count is the index of the first entry above it (n if none).
-__device__ __forceinline__ int window_below(const float* w, int n, float xh, float xl) {
-    int below = 0;
-    if (n == 16) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 t4 = __ldcg(reinterpret_cast<const float4*>(w) + q);
-            below += (__fsub_rn(fabsf(t4.x), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.y), xh) > xl ? 0 : 1) +
-                     (__fsub_rn(fabsf(t4.z), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.w), xh) > xl ? 0 : 1);
-        }
-    } else {
-        for (int i = 0; i < n; ++i) below += __fsub_rn(fabsf(__ldcg(w + i)), xh) > xl ? 0 : 1;
-    }
-    return below;
-}
-
-// As window_below, and zmask gets bit i set when entry i carries the zero-weight
-// flag (sign bit), so the caller need not read the chosen entry again.
-__device__ __forceinline__ int window_below_z(const float* w, int n, float xh, float xl, uint32_t& zmask) {
-    int below = 0;
-    uint32_t z = 0;
-    if (n == 16) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 t4 = __ldcg(reinterpret_cast<const float4*>(w) + q);
-            below += (__fsub_rn(fabsf(t4.x), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.y), xh) > xl ? 0 : 1) +
-                     (__fsub_rn(fabsf(t4.z), xh) > xl ? 0 : 1) + (__fsub_rn(fabsf(t4.w), xh) > xl ? 0 : 1);
-            z |= ((__float_as_uint(t4.x) >> 31) | ((__float_as_uint(t4.y) >> 31) << 1) |
-                  ((__float_as_uint(t4.z) >> 31) << 2) | ((__float_as_uint(t4.w) >> 31) << 3))
-                 << (4 * q);
-        }
-    } else {
-        for (int i = 0; i < n; ++i) {
-            const float t = __ldcg(w + i);
-            below += __fsub_rn(fabsf(t), xh) > xl ? 0 : 1;
-            z |= (__float_as_uint(t) >> 31) << i;
-        }
-    }
-    zmask = z;
-    return below;
-}
-
 // Quad-cooperative window count.  Every lane of the warp calls it at the same
 // point (the shuffles span the full warp).  Each lane brings a window of n <= 16
 // monotone entries at w (16-byte aligned; n = 0: none) and its target
@@ -530,6 +396,85 @@ __device__ __forceinline__ int quad_window_below(const float* w, int n, float xh
     }
     zmask = zmine;
     return mine;
+}
+
+// One multinomial draw of a filter whose tiles' cumulative weights v are in
+// global memory (L2) and whose every 16th |v| (and each tile's last one) is
+// in shared memory: tile search in the table, then a search in the tile's
+// coarse samples for the first window of 16 elements whose last sample exceeds
+// the tile-local target, then that window read whole (64 bytes, 16-byte
+// aligned, quad-cooperatively: every lane of the warp must call it) and the
+// first element above the target counted in registers.  Same predicate on the
+// same monotone sequence as the plain search, so the same result; one 64-byte
+// read from L2 per draw instead of a dozen.
+constexpr int kWinShift = 4;
+constexpr int kWin = 1 << kWinShift;
+__device__ __forceinline__ int32_t multinomial_draw_windowed(uint32_t x, const TableEntry* table, int T,
+                                                             const float* v, const float* coarse, int cpt, int tile,
+                                                             int64_t PA, int lead, float Wh, float Wl) {
+    float uh, ul;
+    u32_pair(x, uh, ul);
+    const float th = __fmul_rn(uh, Wh);
+    const float tl = __fmaf_rn(uh, Wl, __fmaf_rn(ul, Wh, __fmaf_rn(uh, Wh, -th)));
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const float d = __fadd_rn(__fsub_rn(table[mid].bhi, th), __fsub_rn(table[mid].blo, tl));
+        if (d <= 0.f) lo = mid;
+        else hi = mid - 1;
+    }
+    while (lo > 0 && table[lo].il < 0) --lo;
+    const TableEntry e = table[lo];
+    float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
+    float xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
+    if (xh + xl < 0.f) {
+        xh = 0.f;
+        xl = 0.f;
+    }
+    const int64_t b0 = (int64_t)lo * tile;
+    const int nt = (int)min((int64_t)tile, PA - b0);
+    // coarse: first window whose last sample is above the target
+    const float* c = coarse + lo * cpt;
+    int cl = 0, cn = (nt + kWin - 1) >> kWinShift;
+    while (cn > 0) {
+        const int half = cn >> 1;
+        if (__fsub_rn(c[cl + half], xh) > xl) {
+            cn = half;
+        } else {
+            cl += half + 1;
+            cn -= half + 1;
+        }
+    }
+    // the window is read quad-cooperatively: every lane of the warp comes here
+    // (wn = 0 where the target lies past the tile's samples)
+    const int w0 = cl << kWinShift;
+    const int wn = w0 < nt ? min(kWin, nt - w0) : 0;
+    uint32_t zmask;
+    const int below = quad_window_below(v + b0 + w0, wn, xh, xl, zmask);  // elements at or below the target
+    int idx = e.il;
+    if (below < wn) {
+        idx = w0 + below;
+        if ((zmask >> below) & 1u) {  // rounding landed on a zero weight: the next positive one
+            int f = e.il;
+            for (int z = idx + 1; z < nt; ++z)
+                if (!zero_flag(__ldcg(v + b0 + z))) {
+                    f = z;
+                    break;
+                }
+            idx = f;
+        }
+    }
+    return (int32_t)(b0 + idx - lead);
+}
+
+// Every 16th |v| of a tile (and its last one), from this thread's elements,
+// into the tile's coarse samples (shared memory).
+__device__ __forceinline__ void write_tile_coarse(const TileThread& th, int n, float* c) {
+#pragma unroll
+    for (int i = 0; i < kMaxPerThread; ++i) {
+        const int e = th.e0 + i;
+        if (i < th.K && e < n && (((e + 1) & (kWin - 1)) == 0 || e == n - 1)) c[e >> kWinShift] = fabsf(th.v[i]);
+    }
 }
 
 // Tile lookup of the single-launch multinomial draws: lut[k], k = 0..kLut, is

@@ -260,7 +260,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
 
         if (KIND == KIND_MULTI) {
             const int64_t nq = (Pf + 3) >> 2;  // four draws per Philox block
-            for (int64_t q = tid; q < nq; q += kThreads) {
+            // the same number of passes in every thread (the windowed draws read
+            // quad-cooperatively); a lane past the end redraws block 0
+            for (int64_t q0 = 0; q0 < nq; q0 += kThreads) {
+                const bool mine = q0 + tid < nq;
+                if (!__any_sync(0xffffffffu, mine)) continue;  // the whole warp is past the end
+                const int64_t q = mine ? q0 + tid : 0;
                 const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
                 int32_t a[4];
                 if (Tf == 1) {
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                 }
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
-                    if (4 * q + s < Pf) p.anc[4 * q + s] = a[s];
+                    if (mine && 4 * q + s < Pf) p.anc[4 * q + s] = a[s];
             }
             __syncthreads();
             trace_stamp(bp.trace, bp.trace_cap, ticket, 4);
