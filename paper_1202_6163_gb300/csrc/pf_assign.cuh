@@ -344,24 +344,27 @@ __device__ __forceinline__ void multinomial_draws4(const u32x4& r, const TableEn
 
 // Quad-cooperative window count.  Every lane of the warp calls it at the same
 // point (the shuffles span the full warp).  Each lane brings a window of n <= 16
-// monotone entries at w (16-byte aligned; n = 0: none) and its target
-// (xh, xl); the four lanes of each aligned quad read each other's windows, one
-// 16-byte piece per lane, so one load instruction touches the lines of 8
-// windows instead of 32 scattered pieces.  Returns the count of this lane's
-// window entries at or below its target and, in zmask, the window's
-// zero-weight flags (sign bits, bit i for entry i).
-__device__ __forceinline__ int quad_window_below(const float* w, int n, float xh, float xl, uint32_t& zmask) {
+// monotone entries at base + off (base the same in every lane, base + off
+// 16-byte aligned; n = 0: none) and its target (xh, xl); the four lanes of each
+// aligned quad read each other's windows, one 16-byte piece per lane, so one
+// load instruction touches the lines of 8 windows instead of 32 scattered
+// pieces.  Returns the count of this lane's window entries at or below its
+// target and (FLAGS) the window's zero-weight flags in zmask (sign bits, bit i
+// for entry i).
+template <bool FLAGS>
+__device__ __forceinline__ int quad_window_below(const float* base, int off, int n, float xh, float xl,
+                                                 uint32_t& zmask) {
     const int lane = threadIdx.x & 31, q = lane & 3;
     // all four pieces are requested before any is used, so their latencies overlap
-    float t[4][4];
-    int nr[4];
+    float t[4][4], hr[4], lr[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int src = (lane & ~3) | r;
-        const float* wr = reinterpret_cast<const float*>(
-            __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(w), src));
-        nr[r] = __shfl_sync(0xffffffffu, n, src);
-        if (4 * q + 3 < nr[r]) {
+        const float* wr = base + __shfl_sync(0xffffffffu, off, src);
+        const int nr = __shfl_sync(0xffffffffu, n, src);
+        hr[r] = __shfl_sync(0xffffffffu, xh, src);
+        lr[r] = __shfl_sync(0xffffffffu, xl, src);
+        if (4 * q + 3 < nr) {
             const float4 t4 = __ldcg(reinterpret_cast<const float4*>(wr + 4 * q));
             t[r][0] = t4.x;
             t[r][1] = t4.y;
@@ -369,33 +372,32 @@ __device__ __forceinline__ int quad_window_below(const float* w, int n, float xh
             t[r][3] = t4.w;
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) t[r][i] = 4 * q + i < nr[r] ? __ldcg(wr + 4 * q + i) : INFINITY;
+            for (int i = 0; i < 4; ++i) t[r][i] = 4 * q + i < nr ? __ldcg(wr + 4 * q + i) : INFINITY;
         }
     }
-    int mine = 0;
-    uint32_t zmine = 0;
+    // this lane's share of each window: count in bits 0-4, flags from bit 5 (the
+    // lanes' flag bits are disjoint, so adding shares also merges the flags)
+    int part[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const int src = (lane & ~3) | r;
-        const float hr = __shfl_sync(0xffffffffu, xh, src), lr = __shfl_sync(0xffffffffu, xl, src);
         int cnt = 0;
         uint32_t z = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            cnt += __fsub_rn(fabsf(t[r][i]), hr) > lr ? 0 : 1;  // +inf padding counts as above
-            z |= (__float_as_uint(t[r][i]) >> 31) << (4 * q + i);
+            cnt += __fsub_rn(fabsf(t[r][i]), hr[r]) > lr[r] ? 0 : 1;  // +inf padding counts as above
+            if (FLAGS) z |= (__float_as_uint(t[r][i]) >> 31) << (4 * q + i);
         }
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, 1);
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, 2);
-        z |= __shfl_xor_sync(0xffffffffu, z, 1);
-        z |= __shfl_xor_sync(0xffffffffu, z, 2);
-        if (q == r) {
-            mine = cnt;
-            zmine = z;
-        }
+        part[r] = cnt + (int)(z << 5);
     }
-    zmask = zmine;
-    return mine;
+    // transposed sum over the quad: lane q ends with window q's total
+    const bool odd = q & 1, high = q & 2;
+    int s0 = odd ? part[1] : part[0], s1 = odd ? part[3] : part[2];  // windows q&1 and 2 + (q&1)
+    s0 += __shfl_xor_sync(0xffffffffu, odd ? part[0] : part[1], 1);
+    s1 += __shfl_xor_sync(0xffffffffu, odd ? part[2] : part[3], 1);
+    int mine = high ? s1 : s0;
+    mine += __shfl_xor_sync(0xffffffffu, high ? s0 : s1, 2);
+    zmask = FLAGS ? ((uint32_t)mine >> 5) : 0u;
+    return mine & 31;
 }
 
 // One multinomial draw of a filter whose tiles' cumulative weights v are in
@@ -450,7 +452,7 @@ __device__ __forceinline__ int32_t multinomial_draw_windowed(uint32_t x, const T
     const int w0 = cl << kWinShift;
     const int wn = w0 < nt ? min(kWin, nt - w0) : 0;
     uint32_t zmask;
-    const int below = quad_window_below(v + b0 + w0, wn, xh, xl, zmask);  // elements at or below the target
+    const int below = quad_window_below<true>(v, (int)(b0 + w0), wn, xh, xl, zmask);  // elements at or below the target
     int idx = e.il;
     if (below < wn) {
         idx = w0 + below;
@@ -617,10 +619,10 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
     }
     // level 2: the block of 16 samples, then level 3: the 16 elements
     uint32_t zmask;
-    m2 += quad_window_below(c2t + m2, has ? min(16, n2 - m2) : 0, xh, xl, zmask);
+    m2 += quad_window_below<false>(c2, lo * cpt2 + m2, has ? min(16, n2 - m2) : 0, xh, xl, zmask);
     const int w0 = m2 << 4;
     const int wn = has ? min(16, nt - w0) : 0;
-    const int below = quad_window_below(v + b0 + w0, wn, xh, xl, zmask);
+    const int below = quad_window_below<true>(v, (int)(b0 + w0), wn, xh, xl, zmask);
     int idx = e.il;
     if (has) {
         idx = w0 + below;
