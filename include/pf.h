@@ -261,10 +261,12 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream);
  * kept per (device, kind, size class ceil(log2 P)) in this process.
  *
  * pf_autotune times `kind` on the caller's log-weights for each candidate
- * min_tile in {1024, 1536, 2048, 3072, 4096, 6144, 8192} (2 warm-up calls and
- * `reps` timed calls each, CUDA events on `stream`, median), keeps the fastest
- * for P's size class and returns it in *min_tile_out (and its median time in
- * microseconds in *us_out; either may be NULL).  Synchronous; overwrites
+ * min_tile in {1024, 1536, 2048, 3072, 4096, 6144, 8192} (2 warm-up calls,
+ * then three batches of `reps` back-to-back calls each timed by one pair of
+ * CUDA events on `stream`; the median batch mean per call), keeps the fastest
+ * for P's size class and returns it in *min_tile_out (and its time per call in
+ * microseconds in *us_out; either may be NULL).  Candidates that give the same
+ * tiling (P / resident CTAs above them) time alike.  Synchronous; overwrites
  * `ancestors`; arguments as pf_resample_systematic, 1 <= reps <= 1000.
  * PF_ERR_INVALID while `stream` is capturing a graph.  While it runs, other
  * calls of the same kind and size class on the device use the candidate being

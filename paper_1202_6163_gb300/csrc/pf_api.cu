@@ -687,19 +687,22 @@ pf_status pf_autotune(int kind, const float* logw, int64_t P, int32_t* ancestors
             std::lock_guard<std::mutex> lk(g_mu);
             g_min_tile[dev][kind][cls] = c;
         }
+        // two warm-up calls, then three batches of `reps` back-to-back calls
+        // between one event pair: the device clock behind events ticks in
+        // microsecond steps, too coarse to time one call
         times.clear();
-        for (int r = 0; r < reps + 2 && st == PF_OK; ++r) {
+        for (int r = 0; r < 2 && st == PF_OK; ++r) st = resample_cumulative(kind, logw, P, (uint64_t)r, ancestors, stream);
+        for (int b = 0; b < 3 && st == PF_OK; ++b) {
             e = cudaEventRecord(ev[0], s);
-            if (e == cudaSuccess) {
-                st = resample_cumulative(kind, logw, P, (uint64_t)r, ancestors, stream);
-                if (st) break;
-                e = cudaEventRecord(ev[1], s);
-            }
+            for (int r = 0; r < reps && e == cudaSuccess && st == PF_OK; ++r)
+                st = resample_cumulative(kind, logw, P, (uint64_t)(b * reps + r), ancestors, stream);
+            if (st) break;
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
             if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
             float ms = 0.0f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
             if (e != cudaSuccess) st = cuda_fail(e, "autotune timing");
-            if (r >= 2) times.push_back(ms * 1e3f);  // two warm-up calls per candidate
+            times.push_back(ms * 1e3f / (float)reps);
         }
         if (st) break;
         std::sort(times.begin(), times.end());

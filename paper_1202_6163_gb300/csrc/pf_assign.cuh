@@ -9,7 +9,13 @@
 namespace pf {
 
 enum { KIND_MULTI = 0, KIND_STRAT = 1, KIND_SYS = 2 };
-constexpr int kIoCap = 8192;  // staging entries of the run-length decode
+// Staging entries of the run-length decode (per buffer): a chunk holds up to
+// CAP - 4 offsets.  kIoCap serves tiles of up to 8192 elements, whose offset
+// count varies around the tile length, so such a tile nearly always decodes
+// in one chunk; kIoCapSmall serves tiles of up to 4096.
+constexpr int kIoCap = 10240;
+constexpr int kIoCapSmall = 8192;
+static_assert(kIoCap % (4 * 512) == 0 && kIoCapSmall % (4 * 512) == 0, "decode chunks use 4-entry groups per thread");
 
 struct TableEntry {  // multinomial: one tile's lower boundary and scale
     float bhi, blo;  // B_t as a float pair (units of 2^K)
@@ -90,8 +96,9 @@ constexpr int kLocalBits = 13;  // tile-local element index
 static_assert(kTileMax <= (1 << kLocalBits), "element index must fit the tag's low bits");
 constexpr uint32_t kEpochMax = (1u << (31 - kLocalBits)) - 1;  // tags stay positive as int32
 
+template <int CAP>
 __device__ __forceinline__ void stage_init(int32_t* stage) {  // stage: 16-byte aligned
-    for (int i = threadIdx.x; i < 2 * kIoCap / 4; i += kThreads)
+    for (int i = threadIdx.x; i < 2 * CAP / 4; i += kThreads)
         reinterpret_cast<int4*>(stage)[i] = make_int4(-1, -1, -1, -1);
 }
 
@@ -123,15 +130,12 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
         }
     }
     __syncthreads();
-    int4 r[S / 4];
+    // pass A: this thread's maximum, then the exclusive maximum over the block
     int run = -1;
 #pragma unroll
     for (int q = 0; q < S / 4; ++q) {
-        r[q] = *reinterpret_cast<const int4*>(&out[x0i + 4 * q]);
-        r[q].x = run = max(run, r[q].x);
-        r[q].y = run = max(run, r[q].y);
-        r[q].z = run = max(run, r[q].z);
-        r[q].w = run = max(run, r[q].w);
+        const int4 v = *reinterpret_cast<const int4*>(&out[x0i + 4 * q]);
+        run = max(run, max(max(v.x, v.y), max(v.z, v.w)));
     }
     int mm = run;
 #pragma unroll
@@ -144,25 +148,31 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
     if (lane == 31) sm.red_n[warp] = mm;
     __syncthreads();
     for (int w = 0; w < warp; ++w) carry = max(carry, sm.red_n[w]);
-    // entries x in [x0i, x0i + S) hold chunk slots x - shift; every slot of
-    // the chunk carries this chunk's tag (its first slot is marked)
+    // pass B: the entries again (the buffer is not written again before the
+    // chunk after next), as running maxima from the carry, stored.  Entries x in
+    // [x0i, x0i + S) hold chunk slots x - shift; every slot of the chunk carries
+    // this chunk's tag (its first slot is marked).
     constexpr int32_t kLocalMask = (1 << kLocalBits) - 1;
     const int lo = max(x0i, shift), hi = min(x0i + S, shift + (c1 - c0));
     if (hi > lo) {
         int32_t* g = p.anc + (jlo + c0 - shift) + x0i;  // 16-byte aligned
-        if (lo == x0i && hi == x0i + S) {
+        const bool whole = lo == x0i && hi == x0i + S;
+        int rr = carry;
 #pragma unroll
-            for (int q = 0; q < S / 4; ++q)
-                *reinterpret_cast<int4*>(g + 4 * q) = make_int4(
-                    tile_base + (max(carry, r[q].x) & kLocalMask), tile_base + (max(carry, r[q].y) & kLocalMask),
-                    tile_base + (max(carry, r[q].z) & kLocalMask), tile_base + (max(carry, r[q].w) & kLocalMask));
-        } else {
-#pragma unroll
-            for (int q = 0; q < S / 4; ++q) {
-                const int v4[4] = {max(carry, r[q].x), max(carry, r[q].y), max(carry, r[q].z), max(carry, r[q].w)};
+        for (int q = 0; q < S / 4; ++q) {
+            const int4 v = *reinterpret_cast<const int4*>(&out[x0i + 4 * q]);
+            int4 a4;
+            a4.x = tile_base + ((rr = max(rr, v.x)) & kLocalMask);
+            a4.y = tile_base + ((rr = max(rr, v.y)) & kLocalMask);
+            a4.z = tile_base + ((rr = max(rr, v.z)) & kLocalMask);
+            a4.w = tile_base + ((rr = max(rr, v.w)) & kLocalMask);
+            if (whole) {
+                *reinterpret_cast<int4*>(g + 4 * q) = a4;
+            } else {
+                const int v4[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int z = 0; z < 4; ++z)
-                    if (x0i + 4 * q + z >= lo && x0i + 4 * q + z < hi) g[4 * q + z] = tile_base + (v4[z] & kLocalMask);
+                    if (x0i + 4 * q + z >= lo && x0i + 4 * q + z < hi) g[4 * q + z] = v4[z];
             }
         }
     }
@@ -171,9 +181,9 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
     // finishing this chunk's reads of sm.red_n
 }
 
-// stage: the two staging buffers (2 * kIoCap entries, stage_init'ed once per
+// stage: the two staging buffers (2 * CAP entries, stage_init<CAP>'ed once per
 // launch); epoch: the chunk counter of the launch, identical in every thread.
-template <int KIND, int KK = 0>  // KK: elements per thread when fixed, 0 = th.K
+template <int KIND, int KK = 0, int CAP = kIoCap>  // KK: elements per thread when fixed, 0 = th.K
 __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_t* stage, uint32_t& epoch,
                                  TileThread& th, const TileSummary& ts, int64_t index0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -232,16 +242,17 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
     const int32_t tile_base = (int32_t)index0;  // particle index of the tile's element 0
 
     // Run-length decode, one staging chunk at a time (decode_chunk); chunks
-    // of at most 2044 / 4092 offsets use 4 / 8 staging entries per thread.
-    constexpr int kChunk = kIoCap - 4;  // offsets per chunk (room for the shift)
+    // of at most 2044 / 4092 / 8188 offsets use 4 / 8 / 16 staging entries per
+    // thread, larger ones 20.
+    constexpr int kChunk = CAP - 4;  // offsets per chunk (room for the shift)
     for (int c0 = 0; c0 < noff; c0 += kChunk) {
         if (++epoch > kEpochMax) {  // tags exhausted (uniform): clear both buffers and restart
             __syncthreads();
-            stage_init(stage);
+            stage_init<CAP>(stage);
             __syncthreads();
             epoch = 1;
         }
-        int32_t* out = stage + (epoch & 1u) * kIoCap;
+        int32_t* out = stage + (epoch & 1u) * CAP;
         const int32_t tag = (int32_t)(epoch << kLocalBits);
         const int c1 = min(noff, c0 + kChunk);
         const int shift = (int)(((uintptr_t)(p.anc + jlo + c0) >> 2) & 3u);  // to a 16-byte boundary
@@ -250,8 +261,11 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
             decode_chunk<4, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
         else if (need <= 8 * kThreads)
             decode_chunk<8, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
-        else
+        else if (CAP == 16 * kThreads || need <= 16 * kThreads)
             decode_chunk<16, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
+        else
+            decode_chunk<(CAP > 16 * kThreads ? CAP : 16 * kThreads + 4) / kThreads, KK>(
+                p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
     }
 }
 

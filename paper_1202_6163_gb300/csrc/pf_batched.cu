@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
     const int n_items = (int)ld_relaxed_u32(bp.ctl + CTL_ITEMS);
     TileThread th;
     uint32_t chunks = 0;  // staging chunks decoded by this CTA
-    if (KIND != KIND_MULTI) stage_init(reinterpret_cast<int32_t*>(region));  // before the first ticket's barriers
+    if (KIND != KIND_MULTI) stage_init<kIoCap>(reinterpret_cast<int32_t*>(region));  // before the first ticket's barriers
     for (;;) {
         if (tid == 0) sm.f = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
         __syncthreads();

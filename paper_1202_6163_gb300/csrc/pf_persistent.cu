@@ -46,9 +46,14 @@ struct PersistShared {
 // table[T], the tile lookup int lut[kLut + 1] and the level-1 samples
 // float c1[T * cpt1] (sized by the launch).
 
-__host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T) {
+// Staging entries per buffer for KK elements per thread: tiles of up to 4096
+// elements (KK <= 8) need fewer, and the smaller buffers keep more of the SM's
+// shared memory as L1.
+__host__ __device__ constexpr int stage_cap(int KK) { return KK == 16 ? kIoCap : kIoCapSmall; }
+
+__host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T, int KK) {
     return sizeof(PersistShared) + (kind == KIND_MULTI ? (size_t)T * sizeof(TableEntry) + (kLut + 1) * sizeof(int)
-                                                       : 2 * kIoCap * sizeof(int32_t));
+                                                       : 2 * (size_t)stage_cap(KK) * sizeof(int32_t));
 }
 
 // ---------------------------------------------------------------------------
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     }
 
     static_assert(sizeof(PersistShared) % 16 == 0, "the staging buffers are 16-byte aligned");
-    if (KIND != KIND_MULTI) stage_init(reinterpret_cast<int32_t*>(region));  // before pass 2's barriers
+    if (KIND != KIND_MULTI) stage_init<stage_cap(KK)>(reinterpret_cast<int32_t*>(region));  // before pass 2's barriers
 
     // pass 1: scan and record every owned tile
     TileThread th;
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
             ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, (int)min((int64_t)p.tile, PA - t0), sm.tile, th);
         if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], ts.k);
         __syncthreads();
-        assign_offspring<KIND, KK>(p, sm.as, stage, chunks, th, ts, t0 - p.lead);
+        assign_offspring<KIND, KK, stage_cap(KK)>(p, sm.as, stage, chunks, th, ts, t0 - p.lead);
     }
     if (p.trace) {
         __syncthreads();
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
 template <int KIND, int KK>
 static cudaError_t set_smem_attr() {
     return cudaFuncSetAttribute(k_persistent<KIND, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)persistent_smem_bytes(KIND, kMaxTilesTotal));
+                                (int)persistent_smem_bytes(KIND, kMaxTilesTotal, KK));
 }
 
 template <int KIND, int KK>
@@ -298,7 +303,7 @@ static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) 
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes =
-        persistent_smem_bytes(KIND, p.n_tiles) + (p.c2_out ? (size_t)p.n_tiles * p.cpt1 * sizeof(float) : 0);
+        persistent_smem_bytes(KIND, p.n_tiles, KK) + (p.c2_out ? (size_t)p.n_tiles * p.cpt1 * sizeof(float) : 0);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -332,22 +337,19 @@ cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, 
 // Resident CTAs per SM of kind's kernels at the largest shared-memory size a
 // launch may ask for (the smallest over the three per-thread widths; raises
 // their dynamic shared memory limits on the way).  Called once per device.
+template <int KIND, int KK>
+static int blocks_per_sm_kk() {
+    int nb = 0;
+    if (set_smem_attr<KIND, KK>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, KK>, kThreads,
+                                                      persistent_smem_bytes(KIND, kMaxTilesTotal, KK)) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
 template <int KIND>
 static int blocks_per_sm_kind() {
-    const size_t smem = persistent_smem_bytes(KIND, kMaxTilesTotal);
-    int best = INT_MAX, nb = 0;
-    if (set_smem_attr<KIND, 4>() != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, 4>, kThreads, smem) != cudaSuccess)
-        return 0;
-    best = min(best, nb);
-    if (set_smem_attr<KIND, 8>() != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, 8>, kThreads, smem) != cudaSuccess)
-        return 0;
-    best = min(best, nb);
-    if (set_smem_attr<KIND, 16>() != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, 16>, kThreads, smem) != cudaSuccess)
-        return 0;
-    return min(best, nb);
+    return min(blocks_per_sm_kk<KIND, 4>(), min(blocks_per_sm_kk<KIND, 8>(), blocks_per_sm_kk<KIND, 16>()));
 }
 
 int persistent_blocks_per_sm(int kind) {
