@@ -36,53 +36,61 @@ struct AssignShared {
 // ---------------------------------------------------------------------------
 // Offspring-count assignment (systematic, stratified).
 // ---------------------------------------------------------------------------
-// Per-tile scalars (thread 0), in float pairs: the tile's offset range and the
-// map from tile-local cumulative weight v to the offset coordinate
-// y = v * inv_rho + x0 (offsets counted from jlo).  P <= 2^25 on this path.
+// Per-tile scalars (lanes 0 and 1 of warp 0), in float pairs: the tile's
+// offset range and the map from tile-local cumulative weight v to the offset
+// coordinate y = v * inv_rho + x0 (offsets counted from jlo).  P <= 2^25 on
+// this path.
+// One end of a tile's offset range: the offsets below boundary B (B_t for
+// the lower end, B_{t+1} for the upper), the same function of B for both, so
+// adjacent tiles share their common end exactly.  A boundary at 0 gives 0 and
+// one at the total mass W gives P.  Lower end (SYS, STRAT): x0 of the map.
 template <int KIND>
-__device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i, i128 Bh_i, int k_tile) {
-    const fpair W = {sm.W_hi, sm.W_lo};
-    const fpair Bl = fixed_to_pair(Bl_i), Bh = fixed_to_pair(Bh_i);
-    const fpair Pp = fast_two_sum((float)p.P, (float)(p.P - (int64_t)(float)p.P));  // P exactly
-    const fpair PW = pair_div(Pp, W);
-    const fpair yl = pair_mul(Bl, PW), yh = pair_mul(Bh, PW);  // B P / W
-    const bool last = Bh_i >= sm.Wt;
-    long long jl, jh;
-    float x0;
+__device__ __forceinline__ long long offsets_below(const SortedParams& p, const AssignShared& sm, fpair PW, i128 B_i,
+                                                   float& x0) {
+    const fpair y = pair_mul(fixed_to_pair(B_i), PW);  // B P / W
+    long long j;
     if (KIND == KIND_SYS) {
         const u32x4 r = philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1);
-        const float u = u23f(r.x);
-        const fpair dl = pair_sub_f(yl, u), dh = pair_sub_f(yh, u);
-        jl = (Bl_i > 0) ? max(0LL, min((long long)p.P, pair_ceil(dl))) : 0;
-        jh = last ? p.P : max(0LL, min((long long)p.P, pair_ceil(dh)));
-        x0 = __fadd_rn(__fsub_rn(dl.hi, (float)jl), dl.lo);  // N(v) = ceil(v * inv_rho + x0)
+        const fpair d = pair_sub_f(y, u23f(r.x));
+        j = B_i <= 0 ? 0 : (B_i >= sm.Wt ? p.P : max(0LL, min((long long)p.P, pair_ceil(d))));
+        x0 = __fadd_rn(__fsub_rn(d.hi, (float)j), d.lo);  // N(v) = ceil(v * inv_rho + x0)
     } else {
-        jl = 0;
-        if (Bl_i > 0) {
-            const long long f = pair_floor(yl);
+        j = 0;
+        if (B_i >= sm.Wt) {
+            j = p.P;
+        } else if (B_i > 0) {
+            const long long f = pair_floor(y);
             if (f >= p.P) {
-                jl = p.P;
+                j = p.P;
             } else {
-                const float frac = __fadd_rn(__fsub_rn(yl.hi, (float)f), yl.lo);
+                const float frac = __fadd_rn(__fsub_rn(y.hi, (float)f), y.lo);
                 const u32x4 r = philox((uint32_t)(f >> 2), 0u, p.filter, TAG_STRAT, p.key0, p.key1);
-                jl = f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0);
+                j = max(0LL, f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0));
             }
         }
-        jh = p.P;
-        if (!last) {
-            const long long f = pair_floor(yh);
-            if (f < p.P) {
-                const float frac = __fadd_rn(__fsub_rn(yh.hi, (float)f), yh.lo);
-                const u32x4 r = philox((uint32_t)(f >> 2), 0u, p.filter, TAG_STRAT, p.key0, p.key1);
-                jh = max(0LL, f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0));
-            }
-        }
-        x0 = __fadd_rn(__fsub_rn(yl.hi, (float)jl), yl.lo);  // y(v) = v * inv_rho + x0
+        x0 = __fadd_rn(__fsub_rn(y.hi, (float)j), y.lo);  // y(v) = v * inv_rho + x0
     }
-    sm.jlo = jl;
-    sm.noff = (int)max(0LL, jh - jl);
-    sm.tau0 = x0;
-    sm.inv_rho = PW.hi * pow2f(k_tile - sm.K);
+    return j;
+}
+
+// The tile's offset range [jlo, jlo + noff) and the map from tile-local
+// cumulative weight to offsets, into sm.  Called by lanes 0 and 1 of warp 0
+// together: lane 0 forms the lower end, lane 1 the upper.
+template <int KIND>
+__device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i, i128 Bh_i, int k_tile) {
+    const bool upper = (threadIdx.x & 31) == 1;
+    const fpair W = {sm.W_hi, sm.W_lo};
+    const fpair Pp = fast_two_sum((float)p.P, (float)(p.P - (int64_t)(float)p.P));  // P exactly
+    const fpair PW = pair_div(Pp, W);
+    float x0;
+    const long long j = offsets_below<KIND>(p, sm, PW, upper ? Bh_i : Bl_i, x0);
+    const long long jh = __shfl_sync(0x3u, j, 1);
+    if (!upper) {
+        sm.jlo = j;
+        sm.noff = (int)max(0LL, jh - j);
+        sm.tau0 = x0;
+        sm.inv_rho = PW.hi * pow2f(k_tile - sm.K);
+    }
 }
 
 // Run-length decode staging: two buffers of kIoCap entries, used by

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                 __syncthreads();
                 if (!sm.skip) {
                     trace_stamp(bp.trace, bp.trace_cap, ticket, 3);
-                    if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
+                    if (tid < 2) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
                     __syncthreads();
                     assign_offspring<KIND>(p, sm.as, stage, chunks, th, ts, t0 - lead);
                     if (bp.trace) {

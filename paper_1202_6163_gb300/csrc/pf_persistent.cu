@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         const int64_t t0 = (int64_t)t * p.tile;
         if (r != t_count - 1)
             ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, (int)min((int64_t)p.tile, PA - t0), sm.tile, th);
-        if (tid == 0) tile_offsets<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], ts.k);
+        if (tid < 2) tile_offsets<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], ts.k);
         __syncthreads();
         assign_offspring<KIND, KK, stage_cap(KK)>(p, sm.as, stage, chunks, th, ts, t0 - p.lead);
     }
