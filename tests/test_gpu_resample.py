@@ -490,3 +490,32 @@ def test_single_filter_calls_in_a_cuda_graph():
         assert pf.pf_get_device_status(s) == pf.PF_OK
         for x, y in zip(anc + [dst, ess], eager):
             assert torch.equal(x, y)
+
+
+def test_trailing_zero_mass_tiles_get_no_offsets():
+    # The systematic uniform of seed 1472623 (filter 0) is 1 - 3 * 2^-24, the
+    # largest that can shift an offset across the boundary at the total mass W;
+    # every tile after the last positive weight has boundary W at both ends and
+    # must receive no offset, whatever the rounding of B P / W.
+    seed = 1472623
+    assert oracle.stream_uniforms(seed, 0, oracle.TAG_SYS, 1)[0] > 1 - 2.0 ** -21
+    rng = np.random.default_rng(12)
+    for P, live in (((1 << 25) - 3, 20_000_000), (131069, 60000)):
+        lw = np.full(P, -np.inf, np.float32)
+        lw[:live] = rng.standard_normal(live).astype(np.float32)
+        a, st = gpu_resample(pf.pf_resample_systematic, lw, seed)
+        assert st == pf.PF_OK
+        assert a.min() >= 0 and a.max() < live
+        rep = check_cumulative("systematic", lw, a, oracle.systematic(lw, seed), seed)
+        assert rep.ok, rep.summary()
+        # the same filter through the batched call (filter 0, key = seed)
+        if P <= 1 << 17:
+            off = np.array([0, P], np.int64)
+            d_off = torch.from_numpy(off).cuda()
+            seeds = torch.tensor([seed], dtype=torch.int64, device="cuda")
+            b = torch.full((P,), -7, dtype=torch.int32, device="cuda")
+            pf.pf_resample_batched(pf.PF_SYSTEMATIC, to_dev(lw), d_off, 1, 0, seeds, b)
+            assert pf.pf_get_device_status() == pf.PF_OK
+            bb = b.cpu().numpy()
+            assert bb.min() >= 0 and bb.max() < live
+            assert check_cumulative("systematic", lw, bb, oracle.systematic(lw, seed), seed).ok
