@@ -198,22 +198,67 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
     const int noff = sm.noff;
     const long long jlo = sm.jlo;
     const float x0 = sm.tau0, ir = sm.inv_rho;
-    // N_i: offsets of the tile below the element's cumulative weight (kept in v[] as int bits)
-    uint32_t cq = 0xffffffffu;
-    u32x4 cw = {0, 0, 0, 0};
-    int last_n = -1;
+    // Stratified: when the tile's strata fit a staging buffer, the block draws
+    // their uniforms once, four per Philox block, into the buffer the next
+    // decode chunk will use (its last readers finished two chunks ago), stored
+    // with the sign bit set so that every entry stays below the decode's tags;
+    // otherwise each thread draws the blocks its elements need.
+    const bool coop = KIND == KIND_STRAT && noff <= CAP;
+    const int32_t* ub = stage + ((epoch + 1u) & 1u) * CAP;
+    if (KIND == KIND_STRAT && coop) {
+        int32_t* uw = stage + ((epoch + 1u) & 1u) * CAP;
+        const long long g0 = jlo >> 2, g1 = (jlo + noff - 1) >> 2;
+        for (long long g = g0 + tid; g <= g1; g += kThreads) {
+            const u32x4 r = philox((uint32_t)g, 0u, p.filter, TAG_STRAT, p.key0, p.key1);
 #pragma unroll
-    for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
-        if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
-            int n;
-            if (th.e0 + i == ts.i_last) {
-                n = noff;
-            } else if (KIND == KIND_SYS) {
-                const float x = __fmaf_rn(th.v[i], ir, x0);
-                n = x <= 0.f ? 0 : (x >= (float)noff ? noff : min(noff, (int)ceilf(x)));
-            } else {
+            for (int s = 0; s < 4; ++s) {
+                const long long j = 4 * g + s;
+                if (j >= jlo && j < jlo + noff)
+                    uw[j - jlo] = (int32_t)(__float_as_uint(u23f(word_of(r, s))) | 0x80000000u);
+            }
+        }
+        __syncthreads();
+    }
+    // N_i: offsets of the tile below the element's cumulative weight (kept in v[] as int bits)
+    int last_n = -1;
+    if (KIND == KIND_SYS || coop) {
+#pragma unroll
+        for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
+            if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
+                int n;
                 const float y = __fmaf_rn(th.v[i], ir, x0);
-                if (y <= 0.f) {
+                if (th.e0 + i == ts.i_last) {
+                    n = noff;
+                } else if (KIND == KIND_SYS) {
+                    n = y <= 0.f ? 0 : (y >= (float)noff ? noff : min(noff, (int)ceilf(y)));
+                } else if (y <= 0.f) {
+                    n = 0;
+                } else {
+                    const float fl = floorf(y);
+                    if (fl >= (float)noff) {
+                        n = noff;
+                    } else {
+                        const float u = __uint_as_float((uint32_t)ub[(int)fl] & 0x7fffffffu);
+                        n = min(noff, (int)fl + (u < y - fl ? 1 : 0));
+                    }
+                }
+                th.v[i] = __int_as_float(n);
+                last_n = n;
+            }
+        }
+    } else {
+        // stratified, strata beyond the staging buffer: each thread draws the
+        // Philox blocks its elements need
+        uint32_t cq = 0xffffffffu;
+        u32x4 cw = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
+            if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
+                int n;
+                const float y = __fmaf_rn(th.v[i], ir, x0);
+                if (th.e0 + i == ts.i_last) {
+                    n = noff;
+                } else if (y <= 0.f) {
                     n = 0;
                 } else {
                     const float fl = floorf(y);
@@ -229,9 +274,9 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
                         n = min(noff, (int)fl + (u23f(word_of(cw, (int)(j & 3))) < y - fl ? 1 : 0));
                     }
                 }
+                th.v[i] = __int_as_float(n);
+                last_n = n;
             }
-            th.v[i] = __int_as_float(n);
-            last_n = n;
         }
     }
     // exclusive running maximum of the threads' last counts: where this thread's first run starts
