@@ -132,38 +132,45 @@ __global__ void __launch_bounds__(kLgThreads) k_lg_step(LgParams p) {
     const float* yf = p.y + (int64_t)f * D;
     const uint32_t c1 = p.t * (uint32_t)G;
 
+    // the filter's arrays; particle indices within a filter fit 32 bits (P < 2^31)
+    const uint32_t Pu = (uint32_t)p.P;
+    float* lw_f = p.lw + base;
+    const int32_t* anc_f = p.anc + base;
+    const float4* xprev_f = reinterpret_cast<const float4*>(p.x_prev + base * D);
+    float4* xnext_f = reinterpret_cast<float4*>(p.x_next + base * D);
+
     // loads first (ancestors, then the rows they select, then old log-weights)
-    int64_t jj[kLgPerThread], src[kLgPerThread];
+    uint32_t jj[kLgPerThread], src[kLgPerThread];
     bool bad_anc = false, bad_w = false;
 #pragma unroll
     for (int k = 0; k < kLgPerThread; ++k) {
-        jj[k] = (int64_t)tile * (kLgThreads * kLgPerThread) + k * kLgThreads + tid;
+        jj[k] = (uint32_t)tile * (kLgThreads * kLgPerThread) + (uint32_t)(k * kLgThreads + tid);
         src[k] = jj[k];
-        if (rf && jj[k] < p.P) {
-            const int32_t q = __ldcs(p.anc + base + jj[k]);
-            if (q < 0 || q >= p.P) bad_anc = true;
-            else src[k] = q;
+        if (rf && jj[k] < Pu) {
+            const int32_t q = __ldcs(anc_f + jj[k]);
+            if (q < 0 || (uint32_t)q >= Pu) bad_anc = true;
+            else src[k] = (uint32_t)q;
         }
     }
     float prev[kLgPerThread];
 #pragma unroll
-    for (int k = 0; k < kLgPerThread; ++k) prev[k] = (!rf && jj[k] < p.P) ? p.lw[base + jj[k]] : 0.0f;
+    for (int k = 0; k < kLgPerThread; ++k) prev[k] = (!rf && jj[k] < Pu) ? lw_f[jj[k]] : 0.0f;
 
     float v[kLgPerThread];
     float m = -INFINITY;
 #pragma unroll
     for (int k = 0; k < kLgPerThread; ++k) {
-        const int64_t j = jj[k];
+        const uint32_t j = jj[k];
         v[k] = -INFINITY;
-        if (j >= p.P) continue;
-        const float4* xi = reinterpret_cast<const float4*>(p.x_prev + (base + src[k]) * D);
-        float4* xo = reinterpret_cast<float4*>(p.x_next + (base + j) * D);
+        if (j >= Pu) continue;
+        const float4* xi = xprev_f + (size_t)src[k] * G;
+        float4* xo = xnext_f + (size_t)j * G;
         float ss = 0.0f;
 #pragma unroll
         for (int g = 0; g < (GS > 0 ? GS : 16); ++g) {
             if (GS == 0 && g >= G) break;
             const float4 x = __ldcs(xi + g);
-            const float4 z = normals4((uint32_t)j, c1 + (uint32_t)g, (uint32_t)f, p.key0, p.key1);
+            const float4 z = normals4(j, c1 + (uint32_t)g, (uint32_t)f, p.key0, p.key1);
             float4 xn;
             xn.x = a * x.x + p.sigma * z.x;
             xn.y = a * x.y + p.sigma * z.y;
@@ -175,7 +182,7 @@ __global__ void __launch_bounds__(kLgThreads) k_lg_step(LgParams p) {
             ss += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
         }
         const float w = prev[k] + (p.c_obs - p.inv2r * ss);
-        p.lw[base + j] = w;
+        lw_f[j] = w;
         if (w != w || w == INFINITY) bad_w = true;
         v[k] = w;
         m = fmaxf(m, w);
