@@ -112,3 +112,18 @@ def test_precision_batched_4096():
         assert mis <= band
         total_mis += mis
         total_n += n
+    # Metropolis, B = 32: most of these filters are staged in shared memory and
+    # decided on their weights (u w_k < w_j); every 16th filter checked in full
+    B = 32
+    pf.pf_resample_batched(pf.PF_METROPOLIS, d_lw, d_off, 4096, B, d_seeds, anc)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    a = anc.cpu().numpy()
+    mis = n = 0
+    for f in range(0, 4096, 16):
+        lo, hi = off[f], off[f + 1]
+        l = lw[lo:hi]
+        rep = check_metropolis(l, B, a[lo:hi], oracle.metropolis(l, B, int(seeds[f]), f), int(seeds[f]), filter_id=f)
+        assert rep.ok, (f, rep.summary())
+        mis += rep.mismatches
+        n += hi - lo
+    print(f"batched 4096 filters | metropolis B=32 | {mis} mismatched chains in {n} | rate {mis / n:.2e}")
