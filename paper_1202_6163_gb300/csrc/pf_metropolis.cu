@@ -35,7 +35,7 @@ __device__ __forceinline__ bool metropolis_accept(float lj, float lk, float u) {
 // B steps of chain i from state (k, lk).  The proposals do not depend on the
 // chain's state, so each group of kAhead steps draws its proposals first and
 // issues all their log-weight loads before resolving the steps in order.
-constexpr int kAhead = 8;
+constexpr int kAhead = 4;
 
 __device__ __forceinline__ void run_chain(const float* __restrict__ lw, uint32_t Pu, uint32_t i, int steps,
                                           uint32_t filter, uint32_t key0, uint32_t key1, uint32_t& k, float& lk) {
