@@ -337,7 +337,9 @@ def run_gpu(args):
                          "peak": round(l2_rate * 32 / 1e9, 1), "frac": round(steps_per_s / l2_rate, 4),
                          "peak_source": "measured random 4-byte L2 read rate x 32-byte sectors "
                                         "(pf_probe_l2_random_reads, same run)",
-                         "note": "one random 4-byte log-weight read (a 32-byte L2 sector) per chain step"})
+                         "note": "one random 4-byte log-weight read (a 32-byte L2 sector) per chain step; the "
+                                 "array is L2-resident, so neither HBM bandwidth nor ALU throughput bounds the "
+                                 "chains: the SMs issue about one such sector request per cycle"})
     headline = breakdown["systematic"]
 
     e2e = run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes) if not args.no_e2e else None
