@@ -202,6 +202,7 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     // tiles are laid out on the 16-byte aligned window that starts `lead` floats before logw
     const int lead = (int)(((uintptr_t)logw >> 2) & 3u);
     const int64_t PA = P + lead;
+    if (PA > PF_MAX_CUMULATIVE) return PF_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
