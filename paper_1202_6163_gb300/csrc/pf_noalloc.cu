@@ -11,6 +11,7 @@
 // runs the same kernel with its scratch in the fixed array below, which exists
 // from the moment the library is loaded on a device until the process exits.
 #include <cstring>
+#include <mutex>
 
 #include "pf.h"
 #include "pf_internal.h"
@@ -40,11 +41,13 @@ struct StaticDevice {
 
 constexpr int kMaxDevices = 64;
 StaticDevice g_static[kMaxDevices];
+std::mutex g_static_mu;  // host threads making their first call at once set up one device once
 
 // Once per device, with that device current.
 pf_status static_setup(StaticDevice*& out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_static_mu);
     StaticDevice& d = g_static[dev];
     if (!d.ready) {
         void* ptr = nullptr;
