@@ -6,7 +6,7 @@ import pytest
 from scipy import stats
 
 import oracle
-from paper_1202_6163_gb300 import pf, workloads
+from paper_1202_6163_gb300 import pf, tuning, workloads
 from parity import check_cumulative
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +64,38 @@ def test_min_tile_table():
     with pytest.raises(pf.PFError):
         pf.pf_autotune(pf.PF_METROPOLIS, torch.zeros(16, device="cuda"), 16,
                        torch.zeros(16, dtype=torch.int32, device="cuda"))
+
+
+def test_tuned_tiles_saved_and_loaded_in_a_later_call(tmp_path):
+    # a pick stored in the JSON file is set again by tuning.load, at the library's
+    # own size classes (pf_get_min_tile reads the table the calls use)
+    path = str(tmp_path / "tiles.json")
+    P = 300000
+    lw = workloads.gaussian_logw(P, 1.0, seed=77)
+    d = torch.from_numpy(lw).cuda()
+    a = torch.empty(P, dtype=torch.int32, device="cuda")
+    try:
+        tile, us = tuning.tune_and_record(path, pf.PF_SYSTEMATIC, d, P, a, reps=5)
+        assert tile in CANDIDATES and us > 0
+        tuning.record(path, tuning.device_key(), pf.PF_MULTINOMIAL, 5000, 6144)
+        for kind, Pk in ((pf.PF_SYSTEMATIC, P), (pf.PF_MULTINOMIAL, 5000)):
+            pf.pf_set_min_tile(kind, Pk, 0)  # as in a fresh process
+        assert pf.pf_get_min_tile(pf.PF_MULTINOMIAL, 5000) == 2048
+        assert tuning.load(path) == 2
+        assert pf.pf_get_min_tile(pf.PF_SYSTEMATIC, P) == tile
+        assert pf.pf_get_min_tile(pf.PF_SYSTEMATIC, 1 << 19) == tile  # the top of P's class
+        assert pf.pf_get_min_tile(pf.PF_SYSTEMATIC, (1 << 18) + 1) == tile  # its bottom
+        assert pf.pf_get_min_tile(pf.PF_SYSTEMATIC, (1 << 19) + 1) == 2048
+        assert pf.pf_get_min_tile(pf.PF_MULTINOMIAL, 4097) == 6144
+        assert pf.pf_get_min_tile(pf.PF_MULTINOMIAL, 4096) == 2048
+        assert tuning.load(path, key="another GPU|1 SMs|sm_00") == 0
+        pf.pf_resample_multinomial(d[:5000], 5000, 0, 8, a)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        rep = check_cumulative("multinomial", lw[:5000], a[:5000].cpu().numpy(), oracle.multinomial(lw[:5000], 8), 8)
+        assert rep.ok, rep.summary()
+    finally:
+        pf.pf_set_min_tile(pf.PF_SYSTEMATIC, P, 0)
+        pf.pf_set_min_tile(pf.PF_MULTINOMIAL, 5000, 0)
 
 
 @pytest.mark.parametrize("lw,eps", [([0.0, -0.5, 1.2, -2.0, 0.3], 0.01), ([0.0, 0.0, 0.0, 1.5], 0.02),
