@@ -9,7 +9,6 @@ the mismatch count is bounded by the number of in-band decisions; with nearly
 uniform weights (s = 0.25 at P = 2^20) the threshold spacing is itself about
 1e-6 and most decisions are in band.  |log Z error| stays below 2e-6.
 """
-import math
 
 import numpy as np
 import pytest

@@ -10,7 +10,6 @@ later pin relies on.
 """
 import ctypes
 import ctypes.util
-import os
 
 import numpy as np
 import pytest
