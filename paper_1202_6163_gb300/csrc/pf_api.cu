@@ -100,13 +100,24 @@ pf_status workspace(cudaStream_t s, size_t scratch, Workspace*& out) {
     Workspace& w = g_ws[{dev, s}];
     if (!w.ctl) {
         if (capturing(s)) return PF_ERR_NOMEM;
-        e = cudaMalloc(&w.ctl, CTL_WORDS * sizeof(uint32_t));
-        if (e != cudaSuccess) return PF_ERR_NOMEM;
-        e = cudaMalloc(&w.slots, 2 * kMaxRecords * sizeof(uint64_t));
-        if (e != cudaSuccess) return PF_ERR_NOMEM;
-        e = cudaMemsetAsync(w.ctl, 0, CTL_WORDS * sizeof(uint32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.slots, 0, 2 * kMaxRecords * sizeof(uint64_t), s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        // stored only once both buffers exist and are cleared, so that a failed
+        // first call leaves no half-made workspace behind for the next one
+        uint32_t* ctl = nullptr;
+        uint64_t* slots = nullptr;
+        if (cudaMalloc(&ctl, CTL_WORDS * sizeof(uint32_t)) != cudaSuccess) return PF_ERR_NOMEM;
+        if (cudaMalloc(&slots, 2 * kMaxRecords * sizeof(uint64_t)) != cudaSuccess) {
+            cudaFree(ctl);
+            return PF_ERR_NOMEM;
+        }
+        e = cudaMemsetAsync(ctl, 0, CTL_WORDS * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, 2 * kMaxRecords * sizeof(uint64_t), s);
+        if (e != cudaSuccess) {
+            cudaFree(slots);
+            cudaFree(ctl);
+            return cuda_fail(e, "cudaMemsetAsync");
+        }
+        w.ctl = ctl;
+        w.slots = slots;
     }
     if (scratch > w.scratch_bytes) {
         if (capturing(s)) return PF_ERR_NOMEM;
@@ -117,8 +128,9 @@ pf_status workspace(cudaStream_t s, size_t scratch, Workspace*& out) {
         w.scratch = nullptr;
         w.scratch_bytes = 0;
         size_t sz = scratch < 4096 ? 4096 : scratch;
-        e = cudaMalloc(&w.scratch, sz);
-        if (e != cudaSuccess) return PF_ERR_NOMEM;
+        void* p = nullptr;
+        if (cudaMalloc(&p, sz) != cudaSuccess) return PF_ERR_NOMEM;
+        w.scratch = p;
         w.scratch_bytes = sz;
     }
     out = &w;
@@ -134,9 +146,14 @@ pf_status ensure_counters(Workspace& w, size_t n, cudaStream_t s) {
     if (w.counters) cudaFree(w.counters);
     w.counters = nullptr;
     w.n_counters = 0;
-    if (cudaMalloc(&w.counters, n * sizeof(uint32_t)) != cudaSuccess) return PF_ERR_NOMEM;
-    e = cudaMemsetAsync(w.counters, 0, n * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    uint32_t* c = nullptr;
+    if (cudaMalloc(&c, n * sizeof(uint32_t)) != cudaSuccess) return PF_ERR_NOMEM;
+    e = cudaMemsetAsync(c, 0, n * sizeof(uint32_t), s);
+    if (e != cudaSuccess) {
+        cudaFree(c);
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    w.counters = c;
     w.n_counters = n;
     return PF_OK;
 }
