@@ -15,18 +15,45 @@ weight-ratio threshold.  Read concretely:
   near-tie decisions (|u_b - r| <= TAU r) in the oracle's replay reaches the
   GPU's final state.
 
-Every excused mismatch is listed; anything else fails.
+Every excused mismatch is listed; anything else fails.  A listed cumulative
+mismatch carries its size: the index gap |a_gpu - a_orc|, the number of
+positive-weight particles strictly between the two picks (0 when the picks are
+adjacent non-empty intervals), and its relative distance max |x_j - theta_b| /
+theta_b.  A listed Metropolis mismatch carries the first step whose decision
+the replay flipped and the number of flips.
 """
 from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
+from typing import NamedTuple
 
 import numpy as np
 
 import oracle
 
 TAU = 1e-6
+
+
+class Excused(NamedTuple):
+    """One cumulative decision the two sides took differently, at a near tie."""
+    j: int          # decision (offset or draw)
+    gpu: int        # GPU pick
+    orc: int        # oracle pick
+    x: float        # normalised position x_j
+    theta: float    # smallest threshold the picks disagree on
+    rel: float      # max |x_j - theta_b| / theta_b over those thresholds
+    gap: int        # |gpu - orc|
+    between: int    # positive-weight particles strictly between the picks
+
+
+class ExcusedChain(NamedTuple):
+    """One Metropolis chain whose final state differs, reached by flipping near ties."""
+    chain: int
+    gpu: int
+    orc: int
+    first_step: int  # first step whose decision the replay flipped
+    flips: int       # near-tie decisions flipped
 
 
 @dataclass
@@ -41,9 +68,28 @@ class ParityReport:
     def ok(self):
         return not self.failures
 
+    @property
+    def worst_rel(self):
+        """Largest relative distance of an excused cumulative mismatch (0 if none)."""
+        return max((e.rel for e in self.excused if isinstance(e, Excused)), default=0.0)
+
+    @property
+    def worst_gap(self):
+        return max((e.gap for e in self.excused if isinstance(e, Excused)), default=0)
+
+    @property
+    def worst_between(self):
+        return max((e.between for e in self.excused if isinstance(e, Excused)), default=0)
+
+    @property
+    def non_adjacent(self):
+        """Excused cumulative mismatches with a positive-weight particle between the picks."""
+        return sum(1 for e in self.excused if isinstance(e, Excused) and e.between > 0)
+
     def summary(self):
         return (f"n={self.n} mismatches={self.mismatches} excused={len(self.excused)} "
-                f"failures={len(self.failures)} in_band_decisions={self.in_band}")
+                f"failures={len(self.failures)} in_band_decisions={self.in_band} "
+                f"worst_rel={self.worst_rel:.2e} worst_gap={self.worst_gap} worst_between={self.worst_between}")
 
 
 def positions(kind: str, lw: np.ndarray, seed: int, filter_id: int = 0) -> np.ndarray:
@@ -91,17 +137,20 @@ def check_cumulative(kind: str, lw, a_gpu, a_orc, seed: int = 0, filter_id: int 
         lo, hi = min(g, o), max(g, o)
         th = theta[lo:hi]
         tie = bool(np.all(np.abs(x[j] - th) <= tau * th)) and lw[g] > -np.inf
-        rec = (int(j), g, o, float(x[j]), float(th.min()) if th.size else float("nan"),
-               float(np.max(np.abs(x[j] - th) / th)) if th.size else float("nan"))
+        rec = Excused(int(j), g, o, float(x[j]), float(th.min()) if th.size else float("nan"),
+                      float(np.max(np.abs(x[j] - th) / th)) if th.size else float("nan"),
+                      hi - lo, int(np.count_nonzero(lw[lo + 1:hi] > -np.inf)))
         (rep.excused if tie else rep.failures).append(rec)
     return rep
 
 
 def _replay(lw64, P, k, props, unifs, b0, flips_left, target, tau):
-    """Depth-first replay of a chain from step b0 in state k; True if target is reachable
-    by flipping at most flips_left near-tie decisions.  The threshold of every step is
-    r = exp(lw_j - lw_k), including r >= 1 (a move the exact rule always takes is a near
-    tie when u lies within tau r of r, i.e. when r < 1 / (1 - tau))."""
+    """Depth-first replay of a chain from step b0 in state k.  Returns the list of
+    steps whose near-tie decisions were flipped to reach target (empty if none were
+    needed), or None if target is not reachable by flipping at most flips_left of them.
+    The threshold of every step is r = exp(lw_j - lw_k), including r >= 1 (a move the
+    exact rule always takes is a near tie when u lies within tau r of r, i.e. when
+    r < 1 / (1 - tau))."""
     for b in range(b0, len(props)):
         j = int(props[b])
         u = float(unifs[b])
@@ -111,11 +160,12 @@ def _replay(lw64, P, k, props, unifs, b0, flips_left, target, tau):
             r = math.exp(d)
             if abs(u - r) <= tau * r:
                 alt = k if acc else j
-                if _replay(lw64, P, alt, props, unifs, b + 1, flips_left - 1, target, tau):
-                    return True
+                rest = _replay(lw64, P, alt, props, unifs, b + 1, flips_left - 1, target, tau)
+                if rest is not None:
+                    return [b] + rest
         if acc:
             k = j
-    return k == target
+    return [] if k == target else None
 
 
 def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TAU, max_flips=3,
@@ -140,6 +190,9 @@ def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TA
             props, unifs = oracle.metropolis_draws(seed, filter_id, P, i, B)
         else:
             props, unifs = draws[0][i], draws[1][i]
-        ok = _replay(lw64, P, i, props, unifs, 0, max_flips, int(a_gpu[q]), tau)
-        (rep.excused if ok else rep.failures).append((i, int(a_gpu[q]), int(a_orc[q])))
+        flips = _replay(lw64, P, i, props, unifs, 0, max_flips, int(a_gpu[q]), tau)
+        if flips:
+            rep.excused.append(ExcusedChain(i, int(a_gpu[q]), int(a_orc[q]), flips[0], len(flips)))
+        else:
+            rep.failures.append((i, int(a_gpu[q]), int(a_orc[q])))
     return rep

@@ -8,6 +8,16 @@ oracle's).  The table is printed.  Every mismatch is an excused near tie
 the mismatch count is bounded by the number of in-band decisions; with nearly
 uniform weights (s = 0.25 at P = 2^20) the threshold spacing is itself about
 1e-6 and most decisions are in band.  |log Z error| stays below 2e-6.
+
+For every excused mismatch the table gives its size: the worst relative
+distance |x - theta| / theta, the worst index gap |a_gpu - a_orc|, the worst
+number of positive-weight particles strictly between the two picks, and how
+many excused mismatches were not between adjacent non-empty intervals.  The
+worst relative distance is held below REL_GUARD, a regression guard well inside
+the rule's 1e-6: the kernels place a threshold with a relative error of order
+1e-8 (FP32 offset coordinates within a tile), so a mismatch far out in the band
+means a kernel lost precision.  For Metropolis the table gives the excused
+chains and the earliest step at which one diverged.
 """
 
 import numpy as np
@@ -19,6 +29,8 @@ from parity import check_cumulative, check_metropolis
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+REL_GUARD = 3e-7  # worst |x - theta| / theta of an excused mismatch
 
 FNS = {"systematic": (pf.pf_resample_systematic, oracle.systematic),
        "stratified": (pf.pf_resample_stratified, oracle.stratified),
@@ -55,6 +67,22 @@ WORKLOADS = [
 ]
 
 
+HEADER = ("workload | resampler | mismatches | rate | worst |x-theta|/theta | worst gap | worst between | "
+          "non-adjacent | log Z error | in-band fraction")
+
+
+def row(label, name, rep, n, dz):
+    return (f"{label} | {name} | {rep.mismatches} | {rep.mismatches / n:.2e} | {rep.worst_rel:.2e} | "
+            f"{rep.worst_gap} | {rep.worst_between} | {rep.non_adjacent} | {dz:.2e} | {rep.in_band / n:.2e}")
+
+
+def metropolis_row(label, rep, n, dz):
+    first = min((e.first_step for e in rep.excused), default=-1)
+    return (f"{label} | metropolis(B=32, {n} chains) | {rep.mismatches} | {rep.mismatches / n:.2e} | "
+            f"first divergent step {first} | max flips {max((e.flips for e in rep.excused), default=0)} | | | "
+            f"{dz:.2e} |")
+
+
 def test_precision_report():
     rows = []
     for label, make in WORKLOADS:
@@ -63,10 +91,9 @@ def test_precision_report():
         assert abs(dz) < 2e-6, (label, dz)
         for name in FNS:
             rep = single(name, lw, seed=17)
-            rate = rep.mismatches / lw.size
             assert rep.mismatches <= rep.in_band, (label, name, rep.summary())
-            worst = max((r[5] for r in rep.excused), default=0.0)
-            rows.append((label, name, rep.mismatches, rate, worst, dz, rep.in_band / lw.size))
+            assert rep.worst_rel <= REL_GUARD, (label, name, rep.summary())
+            rows.append(row(label, name, rep, lw.size, dz))
         # Metropolis, B = 32, on sampled chains
         B = 32
         d = torch.from_numpy(lw).cuda()
@@ -76,11 +103,10 @@ def test_precision_report():
         idx = np.unique(np.random.default_rng(0).integers(0, lw.size, size=min(lw.size, 4000)))
         rep = check_metropolis(lw, B, a.cpu().numpy()[idx], oracle.metropolis(lw, B, 17, chains=idx), 17, chains=idx)
         assert rep.ok, rep.summary()
-        rows.append((label, "metropolis(B=32, sampled)", rep.mismatches, rep.mismatches / idx.size, float("nan"), dz,
-                     float("nan")))
-    print("\nworkload | resampler | mismatches | rate | worst |x-theta|/theta | log Z error | in-band fraction")
+        rows.append(metropolis_row(label, rep, idx.size, dz))
+    print("\n" + HEADER)
     for r in rows:
-        print(f"{r[0]} | {r[1]} | {r[2]} | {r[3]:.2e} | {r[4]:.2e} | {r[5]:.2e} | {r[6]:.2e}")
+        print(r)
 
 
 def test_precision_batched_4096():
@@ -92,22 +118,30 @@ def test_precision_batched_4096():
     d_seeds = torch.from_numpy(seeds.view(np.int64)).cuda()
     anc = torch.empty(lw.size, dtype=torch.int32, device="cuda")
     total_mis, total_n = 0, 0
+    print("\n" + HEADER)
     for name, kind in (("systematic", pf.PF_SYSTEMATIC), ("stratified", pf.PF_STRATIFIED),
                        ("multinomial", pf.PF_MULTINOMIAL)):
         pf.pf_resample_batched(kind, d_lw, d_off, 4096, 0, d_seeds, anc)
         assert pf.pf_get_device_status() == pf.PF_OK
         a = anc.cpu().numpy()
         mis = n = band = 0
+        worst_rel = 0.0
+        worst_gap = worst_between = non_adj = 0
         for f in range(0, 4096, 16):  # every 16th filter in full
             lo, hi = off[f], off[f + 1]
             l = lw[lo:hi]
             rep = check_cumulative(name, l, a[lo:hi], FNS[name][1](l, int(seeds[f]), f), int(seeds[f]), filter_id=f)
             assert rep.ok, (f, rep.summary())
+            assert rep.worst_rel <= REL_GUARD, (f, name, rep.summary())
             mis += rep.mismatches
             band += rep.in_band
             n += hi - lo
-        print(f"batched 4096 filters | {name} | {mis} mismatches in {n} ancestors | rate {mis / n:.2e} "
-              f"| in-band fraction {band / n:.2e}")
+            worst_rel = max(worst_rel, rep.worst_rel)
+            worst_gap = max(worst_gap, rep.worst_gap)
+            worst_between = max(worst_between, rep.worst_between)
+            non_adj += rep.non_adjacent
+        print(f"batched 4096 filters (every 16th) | {name} | {mis} | {mis / n:.2e} | {worst_rel:.2e} | {worst_gap} | "
+              f"{worst_between} | {non_adj} | | {band / n:.2e}")
         assert mis <= band
         total_mis += mis
         total_n += n
@@ -125,4 +159,4 @@ def test_precision_batched_4096():
         assert rep.ok, (f, rep.summary())
         mis += rep.mismatches
         n += hi - lo
-    print(f"batched 4096 filters | metropolis B=32 | {mis} mismatched chains in {n} | rate {mis / n:.2e}")
+    print(f"batched 4096 filters (every 16th) | metropolis B=32 | {mis} mismatched chains in {n} | {mis / n:.2e}")

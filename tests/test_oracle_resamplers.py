@@ -355,3 +355,45 @@ def test_error_metric_ordering():
     assert e_met == pytest.approx(e_multi, rel=0.15)
     # too few steps leaves the sample biased towards the starting particles
     assert e_met_1 > e_met_4 > e_met and e_met_1 > 1.3 * e_multi
+
+
+# ---------------------------------------------------------------- batched loop
+def test_orc_batched_is_the_per_filter_calls_with_their_filter_ids():
+    """The batched oracle resamples filter f on its own slice with key seeds[f] and
+    filter id f: each slice equals the single-filter call with that id, its ancestors
+    are filter-local, a filter of equal weights keeps the systematic identity, the
+    systematic offspring of every filter stay within floor/ceil of P_f w_i / W_f, and
+    two filters with the same weights and seed but different ids draw different
+    streams.  Empty filters are skipped."""
+    rng = np.random.default_rng(7)
+    sizes = [5, 0, 300, 1, 64, 64, 1000]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    lw = rng.standard_normal(int(off[-1])).astype(np.float32)
+    lw[off[3]:off[4]] = 0.5                          # a one-particle filter
+    lw[off[6]:off[7]] = 1.25                         # equal weights
+    lw[off[5]:off[6]] = lw[off[4]:off[5]]            # same weights as filter 4 ...
+    seeds = np.array([3, 9, 11, 2, 5, 5, 8], dtype=np.uint64)  # ... and the same seed
+    single = {0: oracle.multinomial, 1: oracle.stratified, 2: oracle.systematic}
+    for kind in (0, 1, 2, 3):
+        a = oracle.batched(kind, lw, off, 16, seeds)
+        for f in range(len(sizes)):
+            lo, hi = off[f], off[f + 1]
+            if hi == lo:
+                continue
+            seg = lw[lo:hi]
+            want = (oracle.metropolis(seg, 16, int(seeds[f]), f) if kind == 3
+                    else single[kind](seg, int(seeds[f]), f))
+            assert np.array_equal(a[lo:hi], want), (kind, f)
+            assert a[lo:hi].min() >= 0 and a[lo:hi].max() < hi - lo
+        if kind == 2:
+            assert np.array_equal(a[off[6]:off[7]], np.arange(sizes[6]))
+            for f in range(len(sizes)):
+                lo, hi = off[f], off[f + 1]
+                if hi == lo:
+                    continue
+                w = _w(lw[lo:hi])
+                e = (hi - lo) * w / w.sum()
+                o = np.bincount(a[lo:hi], minlength=hi - lo)
+                assert np.all(o >= np.floor(e - 1e-9)) and np.all(o <= np.ceil(e + 1e-9)), f
+        if kind in (0, 3):
+            assert not np.array_equal(a[off[4]:off[5]], a[off[5]:off[6]])

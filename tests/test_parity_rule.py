@@ -35,11 +35,42 @@ def test_near_tie_is_excused_and_listed():
     a_gpu[7] = 21
     rep = check_cumulative("multinomial", lw, a_gpu, a_orc, x=x)
     assert rep.ok and len(rep.excused) == 1 and rep.excused[0][0] == 7
+    e = rep.excused[0]
+    assert (e.gpu, e.orc, e.gap, e.between) == (21, 20, 1, 0)
+    assert 2e-7 < e.rel < 4e-7 and rep.worst_rel == e.rel and rep.non_adjacent == 0
     # the same disagreement with the uniform 1e-5 away is not excused
     x[7] = theta[20] * (1 - 1e-5)
     a_orc = oracle.multinomial_u(lw, x)
     rep = check_cumulative("multinomial", lw, a_gpu, a_orc, x=x)
     assert not rep.ok
+
+
+def test_skipped_particles_between_the_picks_are_counted():
+    # particle 21 holds e^-30 of a unit weight: thresholds theta_20 and theta_21 both lie
+    # within 1e-6 of the position, so a GPU pick of 22 against the oracle's 20 is a near
+    # tie that skips one positive-weight particle (not adjacent), and the report says so
+    P = 64
+    lw = np.random.default_rng(2).standard_normal(P).astype(np.float32)
+    lw[21] = -30.0
+    theta = oracle.normalised_cumsum(lw)
+    x = np.full(P, 0.5)
+    x[7] = theta[20] * (1 - 3e-7)
+    a_orc = oracle.multinomial_u(lw, x)
+    assert a_orc[7] == 20
+    a_gpu = a_orc.copy()
+    a_gpu[7] = 22
+    rep = check_cumulative("multinomial", lw, a_gpu, a_orc, x=x)
+    assert rep.ok and rep.mismatches == 1
+    e = rep.excused[0]
+    assert (e.gap, e.between) == (2, 1) and rep.worst_gap == 2 and rep.worst_between == 1
+    assert rep.non_adjacent == 1
+    # a zero-weight particle in between is not counted
+    lw[21] = -np.inf
+    theta = oracle.normalised_cumsum(lw)
+    x[7] = theta[20] * (1 - 3e-7)
+    a_orc = oracle.multinomial_u(lw, x)
+    rep = check_cumulative("multinomial", lw, a_gpu, a_orc, x=x)
+    assert rep.ok and rep.excused[0].between == 0 and rep.non_adjacent == 0
 
 
 def test_zero_weight_pick_never_excused():
@@ -82,3 +113,5 @@ def test_metropolis_declined_move_to_a_barely_heavier_particle_is_a_near_tie():
         a_gpu[0] = 0
         rep = check_metropolis(lw, 1, a_gpu, a_orc, 0, draws=(prop, unif))
         assert rep.ok == ok and rep.mismatches == 1
+        if ok:  # the excused chain names the step the replay flipped
+            assert (rep.excused[0].chain, rep.excused[0].first_step, rep.excused[0].flips) == (0, 0, 1)
