@@ -217,7 +217,11 @@ pf_status pf_ess(const float* logw, int64_t P, float* ess_out, double* log_sum_o
  *   logw      concatenated log-weights; filter f owns logw[offsets[f] .. offsets[f+1])
  *   offsets   [F+1] int64, device, non-decreasing, offsets[0] = 0
  *   F         1 <= F <= 2^24
- *   B         Metropolis steps (as pf_resample_metropolis, B >= 0 only)
+ *   B         Metropolis steps: B >= 0 steps for every filter; B < 0: each
+ *             filter takes its own B from the bound of Eqs. 1-5 with eps = 0.01
+ *             and its own largest normalised weight (as
+ *             pf_resample_batched_metropolis_bound, which also returns the B
+ *             chosen per filter); ignored by the other kinds
  *   seeds     [F] uint64, device: filter f uses key seeds[f] and filter id f
  *   ancestors concatenated like logw; filter-local indices in [0, P_f)
  * logw and ancestors need 4-byte alignment, offsets and seeds 8-byte.  A
@@ -244,6 +248,29 @@ pf_status pf_resample_batched(int kind, const float* logw, const int64_t* offset
 pf_status pf_resample_batched_masked(int kind, const float* logw, const int64_t* offsets, int F, int B,
                                      const uint64_t* seeds, const int32_t* mask, int32_t* ancestors,
                                      void* stream);
+
+/*
+ * Batched Metropolis resampling in which every filter takes its own step count
+ * from the bias bound (Section 2, last paragraph of the analysis of B: compute
+ * an appropriate B from Eq. 5 and use it throughout the filter).  For filter f
+ * the CTA that resamples it forms w_max = max_i w_i / sum_i w_i from its
+ * log-weights (FP32, compensated sum), then B_f = the smallest B with
+ * lambda^B <= eps (alpha + beta) / max(alpha, beta) exactly as pf_metropolis_B
+ * computes it (FP64 on the device), capped at 2^24; B_f = 2^24 when every
+ * weight of the filter is zero.  The chains then take B_f steps (Philox filter
+ * id f, key seeds[f], as pf_resample_batched).
+ *   eps       0 < eps < 1
+ *   mask      [F] int32, device, or NULL (as pf_resample_batched_masked)
+ *   B_out     [F] int32, device, or NULL: B_f of every resampled filter (out;
+ *             entries of skipped filters are left untouched)
+ * Other arguments and errors as pf_resample_batched with kind PF_METROPOLIS.
+ * Because B_f follows from w_max in FP32, it can differ from the bound of the
+ * exact w_max by one step where the bound lies within ~1e-6 (relative) of an
+ * integer.
+ */
+pf_status pf_resample_batched_metropolis_bound(const float* logw, const int64_t* offsets, int F, double eps,
+                                               const uint64_t* seeds, const int32_t* mask, int32_t* ancestors,
+                                               int32_t* B_out, void* stream);
 
 /*
  * Pre-size the workspace of `stream` for single-filter calls with up to P_max

@@ -227,8 +227,9 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     pf_status st = device_info(dev, info);
     if (st) return st;
     int G, tile, T, R;
-    if (!persistent_layout(PA, info->num_sms * info->persist_per_sm[kind], min_tile_for(dev, kind, P), G, tile, T,
-                           R)) {
+    // at most one CTA per thread of a CTA: the carries read one CTA record per thread
+    const int G_max = std::min(info->num_sms * info->persist_per_sm[kind], kThreads);
+    if (!persistent_layout(PA, G_max, min_tile_for(dev, kind, P), G, tile, T, R)) {
         return PF_ERR_INVALID;  // P beyond kMaxTilesTotal full tiles
     }
     Workspace* w;
@@ -250,6 +251,8 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
         c2_at = ((size_t)PA * sizeof(float) + 255) & ~(size_t)255;
         c1_at = (c2_at + (size_t)T * cpt2 * sizeof(float) + 255) & ~(size_t)255;
         mscratch = c1_at + (size_t)T * cpt1 * sizeof(float);
+    } else if (R > 1) {
+        mscratch = (size_t)PA * sizeof(float);  // cumulative weights of the tiles pass 2 reloads
     }
     st = workspace(s, mscratch, w);
     if (st) return st;
@@ -270,7 +273,7 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     p.wait_ns = g_wait_ns;
     p.skip_tile = (int)g_skip_tile;
     g_skip_tile = -1;
-    p.v_out = kind == PF_MULTINOMIAL ? (float*)w->scratch : nullptr;
+    p.v_out = (kind == PF_MULTINOMIAL || R > 1) ? (float*)w->scratch : nullptr;
     p.c2_out = cpt2 > 0 ? reinterpret_cast<float*>((char*)w->scratch + c2_at) : nullptr;
     p.c1_out = cpt2 > 0 ? reinterpret_cast<float*>((char*)w->scratch + c1_at) : nullptr;
     p.cpt2 = cpt2;
@@ -369,11 +372,13 @@ pf_status pf_ess(const float* logw, int64_t P, float* ess_out, double* log_sum_o
 
 namespace {
 pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, int F, int B, const uint64_t* seeds,
-                           const int32_t* mask, int32_t* ancestors, void* stream) {
+                           const int32_t* mask, int32_t* ancestors, void* stream, double eps = 0.01,
+                           int32_t* B_out = nullptr) {
     if (!logw || !offsets || !seeds || !ancestors || F < 1 || F > (1 << 24)) return PF_ERR_INVALID;
-    if (kind < PF_MULTINOMIAL || kind > PF_METROPOLIS || (kind == PF_METROPOLIS && B < 0)) return PF_ERR_INVALID;
+    if (kind < PF_MULTINOMIAL || kind > PF_METROPOLIS) return PF_ERR_INVALID;
+    if (!(eps > 0.0) || !(eps < 1.0)) return PF_ERR_INVALID;
     if (((uintptr_t)logw & 3u) || ((uintptr_t)ancestors & 3u) || ((uintptr_t)offsets & 7u) ||
-        ((uintptr_t)seeds & 7u) || ((uintptr_t)mask & 3u))
+        ((uintptr_t)seeds & 7u) || ((uintptr_t)mask & 3u) || ((uintptr_t)B_out & 3u))
         return PF_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -417,6 +422,8 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     if (bp.skip_tile >= 0) g_skip_tile = -1;
     bp.trace = g_trace;
     bp.trace_cap = g_trace_cap;
+    bp.B_out = B_out;
+    bp.eps = eps;
     if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
     return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
 }
@@ -431,6 +438,12 @@ pf_status pf_resample_batched_masked(int kind, const float* logw, const int64_t*
                                      const uint64_t* seeds, const int32_t* mask, int32_t* ancestors, void* stream) {
     if (!mask) return PF_ERR_INVALID;
     return resample_batched(kind, logw, offsets, F, B, seeds, mask, ancestors, stream);
+}
+
+pf_status pf_resample_batched_metropolis_bound(const float* logw, const int64_t* offsets, int F, double eps,
+                                               const uint64_t* seeds, const int32_t* mask, int32_t* ancestors,
+                                               int32_t* B_out, void* stream) {
+    return resample_batched(PF_METROPOLIS, logw, offsets, F, -1, seeds, mask, ancestors, stream, eps, B_out);
 }
 
 pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) {

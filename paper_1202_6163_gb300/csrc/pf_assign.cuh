@@ -73,23 +73,44 @@ __device__ __forceinline__ long long offsets_below(const SortedParams& p, const 
     return j;
 }
 
-// The tile's offset range [jlo, jlo + noff) and the map from tile-local
-// cumulative weight to offsets, into sm.  Called by lanes 0 and 1 of warp 0
-// together: lane 0 forms the lower end, lane 1 the upper.
+// A tile's offset range [jlo, jlo + noff) and the map from its tile-local
+// cumulative weight v to offsets: N(v) = ceil(v * ir + x0) (systematic) or the
+// stratum test on y(v) = v * ir + x0 (stratified), offsets counted from jlo.
+struct TileMap {
+    long long jlo;
+    int noff;
+    float x0, ir;
+};
+
+// The map of a tile with boundaries [Bl_i, Bh_i), formed by two lanes of one
+// warp together: the even lane forms the lower end, the odd lane the upper;
+// `mask` names the participating lanes (both lanes of every pair).  Both lanes
+// return the map.
 template <int KIND>
-__device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i, i128 Bh_i, int k_tile) {
-    const bool upper = (threadIdx.x & 31) == 1;
+__device__ __forceinline__ TileMap tile_map_pair(const SortedParams& p, const AssignShared& sm, i128 Bl_i, i128 Bh_i,
+                                                 int k_tile, unsigned mask) {
+    const int lane = threadIdx.x & 31;
+    const bool upper = lane & 1;
     const fpair W = {sm.W_hi, sm.W_lo};
     const fpair Pp = fast_two_sum((float)p.P, (float)(p.P - (int64_t)(float)p.P));  // P exactly
     const fpair PW = pair_div(Pp, W);
     float x0;
     const long long j = offsets_below<KIND>(p, sm, PW, upper ? Bh_i : Bl_i, x0);
-    const long long jh = __shfl_sync(0x3u, j, 1);
-    if (!upper) {
-        sm.jlo = j;
-        sm.noff = (int)max(0LL, jh - j);
-        sm.tau0 = x0;
-        sm.inv_rho = PW.hi * pow2f(k_tile - sm.K);
+    const long long jl = __shfl_sync(mask, j, lane & ~1);
+    const long long jh = __shfl_sync(mask, j, lane | 1);
+    const float x0l = __shfl_sync(mask, x0, lane & ~1);
+    return {jl, (int)max(0LL, jh - jl), x0l, PW.hi * pow2f(k_tile - sm.K)};
+}
+
+// The same for one tile into sm (lanes 0 and 1 of warp 0 together).
+template <int KIND>
+__device__ void tile_offsets(const SortedParams& p, AssignShared& sm, i128 Bl_i, i128 Bh_i, int k_tile) {
+    const TileMap m = tile_map_pair<KIND>(p, sm, Bl_i, Bh_i, k_tile, 0x3u);
+    if (threadIdx.x == 0) {
+        sm.jlo = m.jlo;
+        sm.noff = m.noff;
+        sm.tau0 = m.x0;
+        sm.inv_rho = m.ir;
     }
 }
 
@@ -118,7 +139,8 @@ __device__ __forceinline__ void stage_init(int32_t* stage) {  // stage: 16-byte 
 // out[s + shift] so that out[x] maps to the 16-byte aligned global position
 // gb + x; each thread scans and stores S consecutive entries
 // (S * kThreads >= c1 - c0 + shift).  Ancestor = tile_base + element.
-template <int S, int KK = 0>  // KK: elements per thread when fixed, 0 = th.K
+template <int S, int KK = 0, bool ONE = false>  // KK: elements per thread when fixed, 0 = th.K;
+                                                 // ONE: the chunk is the tile's only one (c0 = 0, c1 = noff)
 __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared& sm, int32_t* out,
                                              const TileThread& th, long long jlo, int c0, int c1, int shift,
                                              int start0, int32_t tile_base, int32_t tag) {
@@ -131,7 +153,8 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
         if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
             const int b = __float_as_int(th.v[i]);
             if (b > a) {
-                if (a >= c0 && a < c1) out[a - c0 + shift] = mark0 + i;
+                if (ONE) out[a + shift] = mark0 + i;  // 0 <= a < b <= noff: inside the only chunk
+                else if (a >= c0 && a < c1) out[a - c0 + shift] = mark0 + i;
                 else if (a < c0 && b > c0) out[shift] = mark0 + i;
             }
             a = b;
@@ -155,25 +178,27 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
     if (lane == 0) carry = -1;
     if (lane == 31) sm.red_n[warp] = mm;
     __syncthreads();
-    for (int w = 0; w < warp; ++w) carry = max(carry, sm.red_n[w]);
+    carry = max(carry, __reduce_max_sync(0xffffffffu, lane < warp ? sm.red_n[lane] : -1));
     // pass B: the entries again (the buffer is not written again before the
     // chunk after next), as running maxima from the carry, stored.  Entries x in
     // [x0i, x0i + S) hold chunk slots x - shift; every slot of the chunk carries
     // this chunk's tag (its first slot is marked).
-    constexpr int32_t kLocalMask = (1 << kLocalBits) - 1;
     const int lo = max(x0i, shift), hi = min(x0i + S, shift + (c1 - c0));
     if (hi > lo) {
         int32_t* g = p.anc + (jlo + c0 - shift) + x0i;  // 16-byte aligned
         const bool whole = lo == x0i && hi == x0i + S;
         int rr = carry;
+        // every filled slot holds tag | element with this chunk's tag, so one
+        // add turns it into the ancestor tile_base + element
+        const int32_t delta = tile_base - tag;
 #pragma unroll
         for (int q = 0; q < S / 4; ++q) {
             const int4 v = *reinterpret_cast<const int4*>(&out[x0i + 4 * q]);
             int4 a4;
-            a4.x = tile_base + ((rr = max(rr, v.x)) & kLocalMask);
-            a4.y = tile_base + ((rr = max(rr, v.y)) & kLocalMask);
-            a4.z = tile_base + ((rr = max(rr, v.z)) & kLocalMask);
-            a4.w = tile_base + ((rr = max(rr, v.w)) & kLocalMask);
+            a4.x = delta + (rr = max(rr, v.x));
+            a4.y = delta + (rr = max(rr, v.y));
+            a4.z = delta + (rr = max(rr, v.z));
+            a4.w = delta + (rr = max(rr, v.w));
             if (whole) {
                 *reinterpret_cast<int4*>(g + 4 * q) = a4;
             } else {
@@ -192,12 +217,12 @@ __device__ __forceinline__ void decode_chunk(const SortedParams& p, AssignShared
 // stage: the two staging buffers (2 * CAP entries, stage_init<CAP>'ed once per
 // launch); epoch: the chunk counter of the launch, identical in every thread.
 template <int KIND, int KK = 0, int CAP = kIoCap>  // KK: elements per thread when fixed, 0 = th.K
-__device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_t* stage, uint32_t& epoch,
-                                 TileThread& th, const TileSummary& ts, int64_t index0) {
+__device__ void assign_offspring(const SortedParams& p, AssignShared& sm, const TileMap map, int32_t* stage,
+                                 uint32_t& epoch, TileThread& th, const TileSummary& ts, int64_t index0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int noff = sm.noff;
-    const long long jlo = sm.jlo;
-    const float x0 = sm.tau0, ir = sm.inv_rho;
+    const int noff = map.noff;
+    const long long jlo = map.jlo;
+    const float x0 = map.x0, ir = map.ir;
     // Stratified: when the tile's strata fit a staging buffer, the block draws
     // their uniforms once, four per Philox block, into the buffer the next
     // decode chunk will use (its last readers finished two chunks ago), stored
@@ -219,29 +244,27 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
         }
         __syncthreads();
     }
-    // N_i: offsets of the tile below the element's cumulative weight (kept in v[] as int bits)
+    // N_i: offsets of the tile below the element's cumulative weight (kept in v[] as int bits).
+    // Systematic: N = min(ceil(y), noff), the conversion rounding up and saturating at 0.
+    // Stratified: with k = floor(y) (saturating at 0, at most noff - 1), N = k + [u_k < y - k],
+    // capped at noff (y - k is exact).  The tile's last positive element takes noff.
     int last_n = -1;
+    const int il = ts.i_last - th.e0;  // this thread's index of the tile's last positive element, if any
     if (KIND == KIND_SYS || coop) {
+        const uint32_t kmax = (uint32_t)max(noff - 1, 0);
 #pragma unroll
         for (int i = 0; i < (KK ? KK : kMaxPerThread); ++i) {
             if ((KK || i < th.K) && ((th.pos >> i) & 1u)) {
-                int n;
                 const float y = __fmaf_rn(th.v[i], ir, x0);
-                if (th.e0 + i == ts.i_last) {
-                    n = noff;
-                } else if (KIND == KIND_SYS) {
-                    n = y <= 0.f ? 0 : (y >= (float)noff ? noff : min(noff, (int)ceilf(y)));
-                } else if (y <= 0.f) {
-                    n = 0;
+                int n;
+                if (KIND == KIND_SYS) {
+                    n = (int)min(__float2uint_ru(y), (uint32_t)noff);
                 } else {
-                    const float fl = floorf(y);
-                    if (fl >= (float)noff) {
-                        n = noff;
-                    } else {
-                        const float u = __uint_as_float((uint32_t)ub[(int)fl] & 0x7fffffffu);
-                        n = min(noff, (int)fl + (u < y - fl ? 1 : 0));
-                    }
+                    const uint32_t k = min(__float2uint_rd(y), kmax);
+                    const float u = __uint_as_float((uint32_t)ub[k] & 0x7fffffffu);
+                    n = min(noff, (int)k + (u < __fsub_rn(y, (float)k) ? 1 : 0));
                 }
+                n = i == il ? noff : n;
                 th.v[i] = __int_as_float(n);
                 last_n = n;
             }
@@ -290,7 +313,7 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
     if (lane == 0) prev = -1;
     if (lane == 31) sm.red_n[warp] = m;
     __syncthreads();
-    for (int w = 0; w < warp; ++w) prev = max(prev, sm.red_n[w]);
+    prev = max(prev, __reduce_max_sync(0xffffffffu, lane < warp ? sm.red_n[lane] : -1));
     const int start0 = max(prev, 0);
     const int32_t tile_base = (int32_t)index0;  // particle index of the tile's element 0
 
@@ -310,7 +333,17 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, int32_
         const int c1 = min(noff, c0 + kChunk);
         const int shift = (int)(((uintptr_t)(p.anc + jlo + c0) >> 2) & 3u);  // to a 16-byte boundary
         const int need = c1 - c0 + shift;
-        if (need <= 4 * kThreads)
+        if (noff <= kChunk) {  // the tile's only chunk
+            if (need <= 4 * kThreads)
+                decode_chunk<4, KK, true>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
+            else if (need <= 8 * kThreads)
+                decode_chunk<8, KK, true>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
+            else if (CAP == 16 * kThreads || need <= 16 * kThreads)
+                decode_chunk<16, KK, true>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
+            else
+                decode_chunk<(CAP > 16 * kThreads ? CAP : 16 * kThreads + 4) / kThreads, KK, true>(
+                    p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
+        } else if (need <= 4 * kThreads)
             decode_chunk<4, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
         else if (need <= 8 * kThreads)
             decode_chunk<8, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
@@ -726,8 +759,9 @@ __device__ __forceinline__ void write_tile_samples(const TileThread& th, int n, 
 // Reloads a tile stored by write_tile_v into th (elements of tile-local
 // indices [0, n)): v from the magnitudes, the positive-weight mask from the
 // sign bits.  Slots at or beyond n are not read.
+template <int KK = 0>  // elements per thread when fixed (the tile was scanned with KK), 0 = from n
 __device__ __forceinline__ void read_tile_v(const float* vg0, int n, TileThread& th) {
-    const int K = per_thread_count(n);
+    const int K = KK ? KK : per_thread_count(n);
     th.K = K;
     th.e0 = threadIdx.x * K;
     const float* vg = vg0 + th.e0;

@@ -206,7 +206,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
                     trace_stamp(bp.trace, bp.trace_cap, ticket, 3);
                     if (tid < 2) tile_offsets<KIND>(p, sm.as, sm.Bown[c], sm.Bown[c + 1], ts.k);
                     __syncthreads();
-                    assign_offspring<KIND>(p, sm.as, stage, chunks, th, ts, t0 - lead);
+                    const TileMap map = {sm.as.jlo, sm.as.noff, sm.as.tau0, sm.as.inv_rho};
+                    // elements per thread as a constant: 16 for full tiles, fewer for small filters
+                    if (th.K == 16)
+                        assign_offspring<KIND, 16>(p, sm.as, map, stage, chunks, th, ts, t0 - lead);
+                    else if (th.K == 8)
+                        assign_offspring<KIND, 8>(p, sm.as, map, stage, chunks, th, ts, t0 - lead);
+                    else
+                        assign_offspring<KIND, 4>(p, sm.as, map, stage, chunks, th, ts, t0 - lead);
                     if (bp.trace) {
                         __syncthreads();
                         trace_stamp(bp.trace, bp.trace_cap, ticket, 4);

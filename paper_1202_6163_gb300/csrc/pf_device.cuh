@@ -258,6 +258,25 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Maximum that propagates NaN (max.NaN): a NaN operand gives NaN.
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// Warp maximum of a float in one integer reduction: the bits of a float map to
+// an int of the same order (negative values have their magnitude bits
+// flipped), so redux.sync's signed maximum is the float maximum.  -inf stays
+// the smallest value; a NaN maps above +inf.
+__device__ __forceinline__ float warp_max_redux(float v) {
+    int b = __float_as_int(v);
+    b ^= (b >> 31) & 0x7fffffff;
+    b = __reduce_max_sync(0xffffffffu, b);
+    b ^= (b >> 31) & 0x7fffffff;
+    return __int_as_float(b);
+}
+
 __device__ __forceinline__ int warp_max_i(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));

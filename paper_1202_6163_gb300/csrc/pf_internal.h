@@ -29,6 +29,8 @@ enum : int {
     CTL_ARRIVE0 = 8,      // arrival counters of the single-launch kernels,
     CTL_ARRIVE1 = 9,      //   used by alternate epochs (one is reset while the other counts)
     CTL_ITEMS = 10,       // work items of the current batched call (written by its plan pass)
+    CTL_ARRIVE2_0 = 11,   // arrival counters of a second grid-wide wait in one launch (binned
+    CTL_ARRIVE2_1 = 12,   //   multinomial draws), alternating by epoch like CTL_ARRIVE0/1
     CTL_WORDS = 16
 };
 
@@ -67,6 +69,9 @@ struct SortedParams {
     int cpt2, cpt1, c1shift;
     uint64_t* trace;     // phase records (kTraceWords words each), or null
     int64_t trace_cap;   // records the trace buffer holds
+    int2* bins;          // multinomial, binned draws: bin_cap (draw, Philox word) entries, else null
+    uint32_t* cursors;   // multinomial, binned draws: one fill counter per tile
+    int64_t bin_cap;
 };
 
 // Batched call: F filters, filter f owns lw[offsets[f] .. offsets[f+1]).
@@ -87,6 +92,8 @@ struct BatchParams {
     int skip_tile;            // test hook: tile skip_tile of every split filter withholds its record (-1: off)
     uint64_t* trace;     // phase records per work item (kTraceWords words each), or null
     int64_t trace_cap;
+    int32_t* B_out;      // Metropolis with B < 0: each filter's chosen step count, or null
+    double eps;          // Metropolis with B < 0: the eps of Eq. 4
 };
 
 // Phase record of a traced CTA or work item: global-timer stamps at the start,
@@ -137,6 +144,13 @@ struct LgParams {
 
 // Kernel launchers (defined in the .cu files; return the launch error).
 cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s);
+// Binned multinomial draws: shared memory of a launch with T tiles of `tile`
+// log-weights, the resident CTAs per SM at that size, the launch, and the bin
+// capacity the kernel needs at most.
+size_t multinomial_binned_smem(int T, int tile);
+int multinomial_binned_blocks_per_sm(size_t smem);
+cudaError_t launch_multinomial_binned(const SortedParams& p, int grid, cudaStream_t s);
+int64_t multinomial_bin_cap(int64_t P, int T);
 int lg_tile();
 cudaError_t launch_lg_init(const LgParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_lg_step(const LgParams& p, cudaStream_t s);

@@ -137,6 +137,77 @@ __device__ void stage_weights(const float* __restrict__ lw, int64_t n, float* w,
     __syncthreads();
 }
 
+// Block-wide: the largest normalised weight w_max = max_i w_i / sum_i w_i of
+// lw[0..n) (Section 2, Eq. 5's w_max), from the staged weights w (STAGED: w_i =
+// exp(lw_i - m), the largest is 1) or from the log-weights in global memory (one
+// pass of running (max, sum) pairs, rescaled as the maximum grows).  Returns
+// 0 when every weight is zero.  red: THREADS/32 floats of shared memory.
+template <int THREADS, bool STAGED>
+__device__ float largest_weight(const float* __restrict__ lw, const float* w, int64_t n, float* red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float m = -INFINITY, sum = 0.f, c = 0.f;
+    for (int64_t q = tid; q < n; q += THREADS) {
+        if (STAGED) {
+            const float y = __fsub_rn(w[q], c);  // compensated sum of the staged weights (max 1)
+            const float t = __fadd_rn(sum, y);
+            c = __fsub_rn(__fsub_rn(t, sum), y);
+            sum = t;
+        } else {
+            const float x = __ldg(lw + q);
+            if (x > m) {
+                sum = (m > -INFINITY ? sum * expf(m - x) : 0.f) + 1.f;
+                m = x;
+            } else if (x > -INFINITY) {
+                sum += expf(x - m);
+            }
+        }
+    }
+    if (STAGED) {
+        sum = __fsub_rn(sum, c);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) red[warp] = sum;
+        __syncthreads();
+        float tot = 0.f;
+        for (int q = 0; q < THREADS / 32; ++q) tot += red[q];
+        __syncthreads();  // red is reused
+        return tot > 0.f ? 1.f / tot : 0.f;
+    }
+    // combine (max, sum) pairs: first the maximum, then every sum rescaled to it
+    const float mw = warp_max(m);
+    if (lane == 0) red[warp] = mw;
+    __syncthreads();
+    float M = red[0];
+    for (int q = 1; q < THREADS / 32; ++q) M = fmaxf(M, red[q]);
+    __syncthreads();
+    float s2 = m > -INFINITY ? sum * expf(m - M) : 0.f;
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    float tot = 0.f;
+    for (int q = 0; q < THREADS / 32; ++q) tot += red[q];
+    __syncthreads();
+    return (M > -INFINITY && tot > 0.f) ? 1.f / tot : 0.f;
+}
+
+// Eq. 5 (Section 2) on the device, in double precision, as pf_metropolis_B
+// computes it on the host: the smallest B with lambda^B <= eps (alpha + beta) /
+// max(alpha, beta), beta = 1/P, alpha = (1 - w_max)/(P w_max), lambda = 1 -
+// alpha - beta; capped at cap (also for w_max = 0).
+__device__ uint32_t bound_B(int64_t P, double w_max, double eps, uint32_t cap) {
+    if (!(w_max > 0.0)) return cap;
+    if (w_max > 1.0) w_max = 1.0;
+    const double beta = 1.0 / (double)P;
+    const double alpha = (1.0 - w_max) / ((double)P * w_max);
+    const double lambda = 1.0 - alpha - beta;
+    const double target = eps * (alpha + beta) / (alpha > beta ? alpha : beta);
+    if (target >= 1.0) return 0;
+    if (lambda <= 0.0) return 1;
+    double b = ceil(log(target) / log(lambda));
+    if (b >= 1.0 && pow(lambda, b - 1.0) <= target) b -= 1.0;
+    if (!(b >= 0.0)) return cap;
+    return b < (double)cap ? (uint32_t)b : cap;
+}
+
 template <bool STAGED>
 __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __restrict__ lw, int64_t P, int B,
                                                               const uint32_t* __restrict__ B_dev, uint32_t key0,
@@ -196,10 +267,11 @@ cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t*
 // ---------------------------------------------------------------------------
 constexpr int kMetroBThreads = 1024;
 constexpr int kMetroBStage = 56 * 1024;  // floats staged per CTA (224 KiB)
+constexpr uint32_t kBatchedBCap = 1u << 24;  // largest step count chosen for B < 0
 
 __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchParams bp) {
     extern __shared__ float wsm[];
-    __shared__ int f_sm;
+    __shared__ int f_sm, f_B;
     __shared__ float red[kMetroBThreads / 32];
     const int tid = threadIdx.x;
     const int n_items = (int)ld_relaxed_u32(bp.ctl + CTL_ITEMS);
@@ -225,18 +297,31 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
             trace_put(bp.trace, bp.trace_cap, ticket, 7, (uint64_t)(bp.items[ticket] & 31));
         }
         if (staged) stage_weights<kMetroBThreads>(lw, Pf, wsm, red, bp.ctl);
-        for (int w = 1; w <= 3; ++w) trace_stamp(bp.trace, bp.trace_cap, ticket, w);
+        for (int w = 1; w <= 2; ++w) trace_stamp(bp.trace, bp.trace_cap, ticket, w);
+        // B < 0: this filter's own step count from Eq. 5 and its largest normalised weight
+        int steps = bp.B;
+        if (bp.B < 0) {
+            const float wmax = staged ? largest_weight<kMetroBThreads, true>(lw, wsm, Pf, red)
+                                      : largest_weight<kMetroBThreads, false>(lw, wsm, Pf, red);
+            if (tid == 0) {
+                f_B = (int)bound_B(Pf, (double)wmax, bp.eps, kBatchedBCap);
+                if (bp.B_out) bp.B_out[f] = f_B;
+            }
+            __syncthreads();
+            steps = f_B;
+        }
+        trace_stamp(bp.trace, bp.trace_cap, ticket, 3);
         const uint64_t seed = bp.seeds[f];
         const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
         const uint32_t Pu = (uint32_t)Pf;
         for (int64_t i = tid; i < Pf; i += kMetroBThreads) {
             uint32_t k = (uint32_t)i;
             if (staged) {
-                run_chain_w(lw, wsm, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k);
+                run_chain_w(lw, wsm, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k);
             } else {
                 float lk = __ldg(lw + i);
                 if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
-                run_chain(lw, Pu, (uint32_t)i, bp.B, (uint32_t)f, key0, key1, k, lk);
+                run_chain(lw, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k, lk);
             }
             bp.anc[off0 + i] = (int32_t)k;
         }

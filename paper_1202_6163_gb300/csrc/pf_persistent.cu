@@ -3,26 +3,34 @@
 // One cooperative launch; every CTA is resident and owns R >= 1 consecutive
 // tiles of log-weights:
 //   1. pass 1, per owned tile: tile scan (pf_tile.cuh) -- the tile's weights,
-//      its local cumulative weights v_i, its sum S_t relative to 2^{k_t} --
-//      and a 16-byte record (k_t, S_t, i_last) in global memory;
+//      its local cumulative weights v_i, its sum S_t relative to 2^{k_t}.
+//      Systematic / stratified: every tile but the last keeps its v_i in
+//      global scratch (the last stays in registers), and the CTA publishes one
+//      32-byte record of its own mass, S_c = sum_t S_t 2^{k_t - k_c} as an
+//      exact 128-bit fixed-point sum relative to its largest tile exponent
+//      k_c.  Multinomial: each tile writes v_i and a 16-byte record
+//      (k_t, S_t, i_last);
 //   2. the CTA arrives on this launch's counter (release) and one thread waits,
 //      with a time limit, until every CTA has arrived;
-//   3. every CTA reads all T records and forms the inter-tile carries
+//   3. carries.  Systematic / stratified: warp 0 reads the G CTA records and
+//      forms the largest exponent K, the mass below this CTA and the total W
+//      = sum_c S_c 2^{k_c - K} (exact integer sums, so every CTA holds the
+//      same bits and W is the scan's own last prefix), then the boundaries of
+//      its own tiles from its own tile sums; two lanes per owned tile then
+//      form each tile's offset range and offset map.  Multinomial: every CTA
+//      reads all T tile records and forms every tile's carry
 //          B_t = sum_{t' < t} S_t' 2^{k_t' - K}
-//      as exact 128-bit fixed-point sums (2^-90 resolution relative to the
-//      largest tile reference 2^K).  Integer sums are exact and associative, so
-//      every CTA holds bit-identical boundaries, and W = B_T is the scan's own
-//      last prefix;
+//      (exact 128-bit fixed point, 2^-90 relative to 2^K) for its tile table;
 //   4. systematic / stratified (Section 2: these schemes yield offspring
-//      counts), per owned tile (re-scanned when R > 1): the tile owns the
-//      offsets j whose position (j + u_j) W / P lies in [B_t, B_{t+1}); each
-//      element counts the offsets below its cumulative weight, N_i, and its
-//      index fills [N_{i-1}, N_i) by a run-length decode in shared memory (mark
-//      run starts, block max-scan), stored with 128-bit writes;
-//      multinomial: the tiles' v_i were written to global memory in pass 1;
-//      the CTA draws a balanced slice of the P uniforms, finds the tile by a
-//      binary search over the boundaries and the element by a binary search in
-//      that tile's v_i.
+//      counts), per owned tile, last first (the others reload their v_i): the
+//      tile owns the offsets j whose position (j + u_j) W / P lies in
+//      [B_t, B_{t+1}); each element counts the offsets below its cumulative
+//      weight, N_i, and its index fills [N_{i-1}, N_i) by a run-length decode
+//      in shared memory (mark run starts, block max-scan), stored with 128-bit
+//      writes;
+//      multinomial: the CTA draws a balanced slice of the P uniforms, finds the
+//      tile by a binary search over the boundaries and the element by a
+//      binary search in that tile's v_i.
 // Every global write is bounded by [0, P) whatever the data; a NaN/+inf or
 // all-zero weight set records PF_ERR_DOMAIN and writes no ancestors.
 #include <climits>
@@ -36,8 +44,12 @@ constexpr int kMaxOwn = 64;  // tiles per CTA
 struct PersistShared {
     TileShared tile;
     AssignShared as;
-    i128 wsum[kWarps];
+    i128 wsum[kWarps], wsum2[kWarps];
     i128 Bown[kMaxOwn + 1];  // boundaries of this CTA's tiles (systematic, stratified)
+    // systematic / stratified: the owned tiles' summaries and offset maps
+    TileMap own_map[kMaxOwn];
+    float own_shi[kMaxOwn], own_slo[kMaxOwn];
+    int own_k[kMaxOwn], own_il[kMaxOwn];
     int red_k[kWarps];
     int ok;
 };
@@ -62,9 +74,9 @@ __host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T, int 
 // Arrive on this epoch's counter with release semantics (after the CTA's
 // records are written) and wait, one thread, bounded, for every CTA.
 __device__ bool arrive_and_wait(const SortedParams& p, PersistShared& sm, bool skip, uint32_t epoch,
-                                uint64_t t_start) {
+                                uint64_t t_start, int counters = CTL_ARRIVE0) {
     const int tid = threadIdx.x;
-    uint32_t* arrive = p.ctl + CTL_ARRIVE0 + (epoch & 1u);
+    uint32_t* arrive = p.ctl + counters + (epoch & 1u);
     if (tid == 0) {
         if (!skip) red_release_add_u32(arrive, 1u);
         int ok = 1;
@@ -156,6 +168,131 @@ __device__ bool carries(const SortedParams& p, PersistShared& sm, TableEntry* ta
 }
 
 // ---------------------------------------------------------------------------
+// Systematic / stratified: one 32-byte record per CTA, carries by warp 0.
+// ---------------------------------------------------------------------------
+// Record of CTA c at slots[4c .. 4c+4): (k_c, flags) then S_c as four 32-bit
+// words, low first; flags bit 0: a NaN/+inf weight, bit 1: positive mass.
+constexpr uint32_t kRecBad = 1u, kRecMass = 2u;
+
+__device__ __forceinline__ i128 i128_of(uint4 w) {
+    return (i128)(((unsigned __int128)(((uint64_t)w.w << 32) | w.z) << 64) | (((uint64_t)w.y << 32) | w.x));
+}
+
+__device__ __forceinline__ i128 warp_sum_i128(i128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+        const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        v += (i128)(((unsigned __int128)h2 << 64) | l2);
+    }
+    return v;
+}
+
+__device__ __forceinline__ i128 shfl_i128(i128 v, int src) {
+    const unsigned long long lo = __shfl_sync(0xffffffffu, (unsigned long long)v, src);
+    const unsigned long long hi = __shfl_sync(0xffffffffu, (unsigned long long)(v >> 64), src);
+    return (i128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// v 2^{-sh} for v >= 0, truncated; sh >= 0.
+__device__ __forceinline__ i128 shr_i128(i128 v, int sh) { return sh >= 127 ? (i128)0 : (v >> sh); }
+
+// Warp 0, after pass 1: the fixed-point mass of each owned tile relative to
+// the CTA's largest exponent k_c (kept for the boundaries), and the CTA record
+// (written by lane 0, before its arrival).  Returns k_c (INT_MIN: no mass).
+__device__ int publish_cta_record(const SortedParams& p, PersistShared& sm, int t_count) {
+    const int lane = threadIdx.x & 31;
+    int kc = INT_MIN;
+    uint32_t bad = 0;
+    for (int r = lane; r < t_count; r += 32) {
+        const float sh = sm.own_shi[r];
+        bad |= !(sh <= 3.402823466e38f);
+        if (sh > 0.f) kc = max(kc, sm.own_k[r]);
+    }
+    kc = warp_max_i(kc);
+    bad = __any_sync(0xffffffffu, bad);
+    i128 a = 0;
+    if (kc != INT_MIN && !bad)
+        for (int r = lane; r < t_count; r += 32)
+            if (sm.own_shi[r] > 0.f) {
+                const int sh = sm.own_k[r] - kc;
+                a += fixed_of(sm.own_shi[r], sh) + fixed_of(sm.own_slo[r], sh);
+            }
+    a = warp_sum_i128(a);
+    if (lane == 0) {
+        uint32_t* rec = reinterpret_cast<uint32_t*>(p.slots) + 8 * blockIdx.x;
+        const unsigned __int128 u = (unsigned __int128)a;
+        st_v4_u32(rec, (uint32_t)kc, (bad ? kRecBad : 0u) | (kc != INT_MIN ? kRecMass : 0u), 0u, 0u);
+        st_v4_u32(rec + 4, (uint32_t)u, (uint32_t)(u >> 32), (uint32_t)(u >> 64), (uint32_t)(u >> 96));
+    }
+    return kc;
+}
+
+// Block-wide, after every CTA arrived: K, W and this CTA's tile boundaries
+// sm.Bown[0 .. t_count] (in units of 2^-90 relative to 2^K) from the G CTA
+// records (one per thread, all loaded at once) and the owned tiles' sums.
+// Tile t's upper boundary is its successor's lower one, also across CTAs
+// (both are B_c plus the same truncated sum), and the last tile's is W.
+// kc: the CTA's own exponent (needed in warp 0 only).  Returns false (and
+// records PF_ERR_DOMAIN) for NaN/+inf or all-zero weights.
+__device__ bool carries_agg(const SortedParams& p, PersistShared& sm, int t_count, int kc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, G = gridDim.x;
+    const uint32_t* rec = reinterpret_cast<const uint32_t*>(p.slots);
+    uint4 h = make_uint4(0, 0, 0, 0), sw = make_uint4(0, 0, 0, 0);
+    if (tid < G) {  // G <= kThreads: one record per thread
+        h = __ldcg(reinterpret_cast<const uint4*>(rec + 8 * tid));
+        sw = __ldcg(reinterpret_cast<const uint4*>(rec + 8 * tid + 4));
+    }
+    // largest exponent with mass, and the domain check
+    const int bad = __syncthreads_or((int)(h.y & kRecBad));
+    const int Kw = __reduce_max_sync(0xffffffffu, (h.y & kRecMass) ? (int)h.x : INT_MIN);
+    if (lane == 0) sm.red_k[warp] = Kw;
+    __syncthreads();
+    const int K = __reduce_max_sync(0xffffffffu, lane < kWarps ? sm.red_k[lane] : INT_MIN);
+    if (K == INT_MIN || bad) {
+        if (tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
+        return false;
+    }
+    // the masses below this CTA and of all CTAs, relative to 2^K
+    const i128 v = (h.y & kRecMass) ? shr_i128(i128_of(sw), K - (int)h.x) : (i128)0;
+    const i128 below_w = warp_sum_i128(tid < (int)blockIdx.x ? v : (i128)0);
+    const i128 all_w = warp_sum_i128(v);
+    if (lane == 0) {
+        sm.wsum[warp] = below_w;
+        sm.wsum2[warp] = all_w;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const i128 below = warp_sum_i128(lane < kWarps ? sm.wsum[lane] : (i128)0);
+        const i128 all = warp_sum_i128(lane < kWarps ? sm.wsum2[lane] : (i128)0);
+        // the owned tiles: exclusive prefix of their fixed-point masses, then shifted to 2^K
+        const int shc = kc == INT_MIN ? 0 : K - kc;
+        i128 run = 0;
+        for (int r0 = 0; r0 <= t_count; r0 += 32) {
+            const int r = r0 + lane;
+            i128 a = 0;
+            if (r < t_count && kc != INT_MIN && sm.own_shi[r] > 0.f) {
+                const int sh = sm.own_k[r] - kc;
+                a = fixed_of(sm.own_shi[r], sh) + fixed_of(sm.own_slo[r], sh);
+            }
+            const i128 inc = warp_scan_i128(a, lane);
+            if (r <= t_count) sm.Bown[r] = below + shr_i128(run + inc - a, shc);
+            run += shfl_i128(inc, 31);
+        }
+        if (lane == 0) {
+            sm.as.K = K;
+            sm.as.Wt = all;
+            const fpair Wp = fixed_to_pair(all);
+            sm.as.W_hi = Wp.hi;
+            sm.as.W_lo = Wp.lo;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Multinomial draws (Figure 1a): binary searches in global units.
 // ---------------------------------------------------------------------------
 __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, const TableEntry* table) {
@@ -205,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
     unsigned char* region = smem_raw + sizeof(PersistShared);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const uint64_t t_start = global_ns();
     const uint32_t epoch = ld_relaxed_u32(p.ctl + CTL_EPOCH) + 1u;
     const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
@@ -236,25 +373,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         const int n = (int)min((int64_t)p.tile, PA - t0);
         ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
         if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
+        skip |= (t == p.skip_tile);
         if (KIND == KIND_MULTI) {
             write_tile_v<KK>(p, th, t0, n);
             if (p.c2_out)
                 write_tile_samples<KK>(th, n, p.c2_out + (int64_t)t * p.cpt2, p.c1_out + (int64_t)t * p.cpt1, p.c1shift);
             __threadfence();
-        }
-        if (tid == 0) {
-            skip |= (t == p.skip_tile);
-            st_v4_u32(rec + 4 * t, (uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo),
-                      (uint32_t)ts.i_last);
+            if (tid == 0)
+                st_v4_u32(rec + 4 * t, (uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi),
+                          __float_as_uint(ts.S.lo), (uint32_t)ts.i_last);
+        } else {
+            if (r + 1 < t_count) write_tile_v<KK>(p, th, t0, n);  // reloaded in pass 2
+            if (tid == 0) {
+                sm.own_k[r] = ts.k;
+                sm.own_il[r] = ts.i_last;
+                sm.own_shi[r] = ts.bad ? NAN : ts.S.hi;
+                sm.own_slo[r] = ts.S.lo;
+            }
         }
         __syncthreads();
     }
+    int kc = 0;
+    if (KIND != KIND_MULTI && warp == 0) kc = publish_cta_record(p, sm, t_count);
 
     trace_stamp(p.trace, p.trace_cap, blockIdx.x, 1);
     bool ok = arrive_and_wait(p, sm, skip, epoch, t_start);
     trace_stamp(p.trace, p.trace_cap, blockIdx.x, 2);
     if (!ok && tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
-    if (ok) ok = carries<KIND>(p, sm, reinterpret_cast<TableEntry*>(region), t_first, t_count);
+    if (ok) {
+        if (KIND == KIND_MULTI) {
+            ok = carries<KIND>(p, sm, reinterpret_cast<TableEntry*>(region), t_first, t_count);
+        } else {
+            ok = carries_agg(p, sm, t_count, kc);
+        }
+    }
     if (ok) trace_stamp(p.trace, p.trace_cap, blockIdx.x, 3);
     // every CTA read the epoch before arriving, and CTA 0 has seen all arrivals
     // (or waited out its limit): reset the counter the next launch will use and
@@ -273,22 +425,370 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         }
         return;
     }
-    // pass 2: offsets of every owned tile (the last tile's scan is still in registers)
+    // the offset maps of every owned tile at once, two lanes per tile
+    if (tid < 2 * ((t_count + 15) & ~15)) {
+        const int r = min(tid >> 1, t_count - 1);
+        const TileMap m = tile_map_pair<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], sm.own_k[r], 0xffffffffu);
+        if ((tid & 1) == 0 && (tid >> 1) < t_count) sm.own_map[tid >> 1] = m;
+    }
+    __syncthreads();
+    // pass 2: offsets of every owned tile (the last tile's scan is still in
+    // registers; the others reload their cumulative weights)
     int32_t* stage = reinterpret_cast<int32_t*>(region);
     uint32_t chunks = 0;  // staging chunks decoded by this CTA
     for (int r = t_count - 1; r >= 0; --r) {
         const int t = t_first + r;
         const int64_t t0 = (int64_t)t * p.tile;
-        if (r != t_count - 1)
-            ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, (int)min((int64_t)p.tile, PA - t0), sm.tile, th);
-        if (tid < 2) tile_offsets<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], ts.k);
-        __syncthreads();
-        assign_offspring<KIND, KK, stage_cap(KK)>(p, sm.as, stage, chunks, th, ts, t0 - p.lead);
+        if (r != t_count - 1) {
+            read_tile_v<KK>(p.v_out + t0, (int)min((int64_t)p.tile, PA - t0), th);
+            ts.i_last = sm.own_il[r];
+        }
+        assign_offspring<KIND, KK, stage_cap(KK)>(p, sm.as, sm.own_map[r], stage, chunks, th, ts, t0 - p.lead);
     }
     if (p.trace) {
         __syncthreads();
         trace_stamp(p.trace, p.trace_cap, blockIdx.x, 4);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Multinomial by binned draws (Figure 1a; the binary search of Section 3, run
+// on draws grouped by tile).  After the tile scan and the carries, each CTA:
+//   2a. counts its slice of the P draws by target tile (shared-memory
+//       counters; the tile of a draw from the table of boundaries);
+//   2r. reserves room for them in each tile's bin with one global atomic per
+//       (CTA, tile);
+//   2b. draws them again and writes (j, Philox word) into its reserved slots;
+//       a draw that finds its bin full (bins hold the tile's expected count
+//       P S_t / W plus six standard deviations plus 32, so this is rare) is
+//       resolved at once by a binary search over the tile's cumulative weights
+//       in global memory;
+// then, after a second grid-wide wait,
+//   3.  takes an equal share of the bin positions, stages the cumulative
+//       weights of each tile it meets in shared memory, and resolves the draws
+//       there: the same lower-bound search on the same monotone sequence as
+//       the direct search, so the same ancestors.
+// ---------------------------------------------------------------------------
+// Shared memory after PersistShared: table[T] (TableEntry), boff[T+1]
+// (bin starts), cnt[T], base[T] (ints, each array padded to 4), then a
+// region used first for the tile lookup lut[kLut+1] and later for one tile's
+// cumulative weights (tile floats).
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
+__host__ __device__ constexpr size_t mb_region_bytes(int tile) {
+    return (size_t)((kLut + 1) * 4 > tile * 4 ? pad4(kLut + 1) * 4 : pad4(tile) * 4);
+}
+size_t multinomial_binned_smem(int T, int tile) {
+    return sizeof(PersistShared) + (size_t)T * sizeof(TableEntry) + (size_t)(pad4(T + 1) + 2 * pad4(T)) * 4 +
+           mb_region_bytes(tile);
+}
+
+int64_t multinomial_bin_cap(int64_t P, int T) {
+    // sum over tiles of lambda_t + 6 sqrt(lambda_t) + 33 <= P + 6 sqrt(P T) + 33 T, plus slack for rounding
+    return P + (int64_t)ceil(6.0 * sqrt((double)P * (double)T)) + 34LL * T + P / 256 + 1024;
+}
+
+// The tile whose cumulative interval holds the target (th, tl): the tiles between
+// the lookup points around the uniform, confirmed (else a full search; the
+// predicate is monotone in t), and never a tile without weight.
+__device__ __forceinline__ int draw_tile(uint32_t x, const TableEntry* table, const int* lut, int T, float th,
+                                         float tl) {
+    const int kq = (int)(x >> (32 - kLutBits));
+    int lo = last_tile_at_or_below(table, lut[kq], min(lut[kq + 1], T - 1), th, tl);
+    if (!boundary_at_or_below(table[lo], th, tl) || (lo + 1 < T && boundary_at_or_below(table[lo + 1], th, tl)))
+        lo = last_tile_at_or_below(table, 0, T - 1, th, tl);
+    while (lo > 0 && table[lo].il < 0) --lo;
+    return lo;
+}
+
+// Tile-local target of (th, tl) in tile entry e (clamped at the tile start).
+__device__ __forceinline__ void local_target(const TableEntry& e, float th, float tl, float& xh, float& xl) {
+    xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
+    xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
+    if (xh + xl < 0.f) {
+        xh = 0.f;
+        xl = 0.f;
+    }
+}
+
+// First element of v[0..n) whose |v| exceeds the tile-local target (xh, xl)
+// (|v| - xh is exact near the decision), moved to the next positive element
+// when rounding lands on a zero weight; il (the tile's last positive element)
+// when none exceeds it.  GLOBAL: v in global memory (L2), else shared.
+template <bool GLOBAL>
+__device__ __forceinline__ int search_tile(const float* v, int n, int il, float xh, float xl) {
+    auto ld = [&](int i) -> float { return GLOBAL ? __ldcg(v + i) : v[i]; };
+    int lo = 0, cnt = n;
+    while (cnt > 0) {
+        const int half = cnt >> 1;
+        if (__fsub_rn(fabsf(ld(lo + half)), xh) > xl) {
+            cnt = half;
+        } else {
+            lo += half + 1;
+            cnt -= half + 1;
+        }
+    }
+    if (lo >= n) return il;
+    if (zero_flag(ld(lo))) {
+        for (int z = lo + 1; z < n; ++z)
+            if (!zero_flag(ld(z))) return z;
+        return il;
+    }
+    return lo;
+}
+
+// Block-wide exclusive prefix sum of a[0..n) in place (n <= 8 * kThreads);
+// a[n] receives the total.  red: kWarps ints.
+__device__ void block_excl_scan(int* a, int n, int* red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int per = 8;
+    int loc[per], sum = 0;
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+        const int k = tid * per + i;
+        loc[i] = k < n ? a[k] : 0;
+        sum += loc[i];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int h = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += h;
+    }
+    if (lane == 31) red[warp] = inc;
+    __syncthreads();
+    int wb = lane < kWarps ? red[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < kWarps; o <<= 1) {
+        const int h = __shfl_up_sync(0xffffffffu, wb, o);
+        if (lane >= o) wb += h;
+    }
+    const int total = __shfl_sync(0xffffffffu, wb, kWarps - 1);
+    int run = (warp > 0 ? __shfl_sync(0xffffffffu, wb, warp - 1) : 0) + inc - sum;
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+        const int k = tid * per + i;
+        if (k < n) a[k] = run;
+        run += loc[i];
+    }
+    if (tid == 0) a[n] = total;
+    __syncthreads();
+}
+
+template <int KK>
+__global__ void __launch_bounds__(kThreads, 2) k_multinomial_binned(SortedParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
+    const int T = p.n_tiles;
+    TableEntry* table = reinterpret_cast<TableEntry*>(smem_raw + sizeof(PersistShared));
+    int* boff = reinterpret_cast<int*>(table + T);
+    int* cnt = boff + pad4(T + 1);
+    int* base = cnt + pad4(T);
+    int* lut = base + pad4(T);
+    float* vt = reinterpret_cast<float*>(lut);  // phase 3: one tile's cumulative weights
+    const int tid = threadIdx.x, cta = blockIdx.x, G = gridDim.x;
+    const uint64_t t_start = global_ns();
+    const uint32_t epoch = ld_relaxed_u32(p.ctl + CTL_EPOCH) + 1u;
+    const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
+    const int t_first = cta * R;
+    const int t_count = max(0, min(R, T - t_first));
+    uint32_t* rec = reinterpret_cast<uint32_t*>(p.slots);
+    if (p.trace) {
+        trace_put(p.trace, p.trace_cap, cta, 0, t_start);
+        for (int w = 1; w <= 4; ++w) trace_put(p.trace, p.trace_cap, cta, w, 0);
+        trace_put(p.trace, p.trace_cap, cta, 5, cta);
+        trace_put(p.trace, p.trace_cap, cta, 6, 0);
+        trace_put(p.trace, p.trace_cap, cta, 7, (uint64_t)t_count);
+    }
+    // 1. scan every owned tile: cumulative weights to global memory, one record per tile
+    TileThread th;
+    const int64_t PA = p.P + p.lead;
+    if (tid < t_count) p.cursors[t_first + tid] = 0u;  // this launch's bins start empty
+    for (int r = 0; r < t_count; ++r) {
+        const int t = t_first + r;
+        const int64_t t0 = (int64_t)t * p.tile;
+        const int n = (int)min((int64_t)p.tile, PA - t0);
+        const TileSummary ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
+        if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
+        write_tile_v<KK>(p, th, t0, n);
+        __threadfence();
+        if (tid == 0)
+            st_v4_u32(rec + 4 * t, (uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo),
+                      (uint32_t)ts.i_last);
+        __syncthreads();
+    }
+    trace_stamp(p.trace, p.trace_cap, cta, 1);
+    bool ok = arrive_and_wait(p, sm, false, epoch, t_start);
+    trace_stamp(p.trace, p.trace_cap, cta, 2);
+    if (!ok && tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
+    if (ok) ok = carries<KIND_MULTI>(p, sm, table, t_first, t_count);
+    if (cta == 0 && tid == 0) {
+        atomicExch(p.ctl + CTL_ARRIVE0 + ((epoch + 1u) & 1u), 0u);
+        atomicExch(p.ctl + CTL_EPOCH, epoch);
+    }
+    if (!ok) return;
+    const float Wh = sm.as.W_hi, Wl = sm.as.W_lo;
+    build_tile_lut(table, T, Wh, Wl, lut, sm.red_k);
+    // bin capacities: the tile's expected count P S_t / W plus 6 sigma plus 32
+    // (every CTA forms the same integers from the same bits), then bin starts
+    for (int t = tid; t < T; t += kThreads) {
+        int cap = 0;
+        if (table[t].il >= 0) {
+            const float nh = t + 1 < T ? table[t + 1].bhi : Wh, nl = t + 1 < T ? table[t + 1].blo : Wl;
+            const float frac = __fdiv_rn(__fadd_rn(__fsub_rn(nh, table[t].bhi), __fsub_rn(nl, table[t].blo)), Wh);
+            const float lam = fmaxf(frac, 0.f) * (float)p.P;
+            cap = (int)fminf(ceilf(lam + 6.f * sqrtf(lam) + 32.f), 2147483647.f / 8.f);
+        }
+        boff[t] = cap;
+        cnt[t] = 0;
+    }
+    __syncthreads();
+    block_excl_scan(boff, T, sm.red_k);
+    const bool binned = (int64_t)boff[T] <= p.bin_cap;  // always, by the bound the host sized the bins with
+    trace_stamp(p.trace, p.trace_cap, cta, 3);
+
+    const int64_t nq = (p.P + 3) >> 2;  // four draws per Philox block
+    const int64_t q_beg = nq * cta / G, q_end = nq * (cta + 1) / G;
+    const float* vg = p.v_out;
+    // 2a. count this CTA's draws by tile
+    if (binned) {
+        for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
+            const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (4 * q + s >= p.P) break;
+                const uint32_t x = word_of(r, s);
+                float uh, ul, th2, tl2;
+                u32_pair(x, uh, ul);
+                draw_target(uh, ul, Wh, Wl, th2, tl2);
+                atomicAdd(&cnt[draw_tile(x, table, lut, T, th2, tl2)], 1);
+            }
+        }
+        __syncthreads();
+        // 2r. one reservation per tile this CTA draws into
+        for (int t = tid; t < T; t += kThreads)
+            if (cnt[t] > 0) base[t] = (int)atomicAdd(p.cursors + t, (uint32_t)cnt[t]);
+        __syncthreads();
+    }
+    // 2b. the draws again, into their slots (or resolved at once when the bin is full)
+    for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
+        const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int64_t j = 4 * q + s;
+            if (j >= p.P) break;
+            const uint32_t x = word_of(r, s);
+            float uh, ul, th2, tl2;
+            u32_pair(x, uh, ul);
+            draw_target(uh, ul, Wh, Wl, th2, tl2);
+            const int t = draw_tile(x, table, lut, T, th2, tl2);
+            if (binned) {
+                const int slot = base[t] + atomicSub(&cnt[t], 1) - 1;
+                if (slot < boff[t + 1] - boff[t]) {
+                    p.bins[boff[t] + slot] = make_int2((int)j, (int)x);
+                    continue;
+                }
+            }
+            float xh, xl;
+            local_target(table[t], th2, tl2, xh, xl);
+            const int64_t b0 = (int64_t)t * p.tile;
+            const int idx = search_tile<true>(vg + b0, (int)min((int64_t)p.tile, PA - b0), table[t].il, xh, xl);
+            p.anc[j] = (int32_t)(b0 + idx - p.lead);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    ok = arrive_and_wait(p, sm, false, epoch, t_start, CTL_ARRIVE2_0);
+    if (cta == 0 && tid == 0) atomicExch(p.ctl + CTL_ARRIVE2_0 + ((epoch + 1u) & 1u), 0u);
+    if (!ok) {
+        if (tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
+        return;
+    }
+    // 3. an equal share of the bin positions; each tile met is staged once
+    if (binned) {
+        const int64_t C = boff[T];
+        const int64_t p0 = C * cta / G, p1 = C * (cta + 1) / G;
+        int lo = 0, hi = T - 1;  // last tile whose bin starts at or before p0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (boff[mid] <= p0) lo = mid;
+            else hi = mid - 1;
+        }
+        __syncthreads();  // lut (aliased by vt) is no longer read
+        for (int t = lo; t < T && (int64_t)boff[t] < p1; ++t) {
+            const int64_t s0 = max(p0, (int64_t)boff[t]);
+            const int64_t filled = min((int64_t)__ldcg(p.cursors + t), (int64_t)(boff[t + 1] - boff[t]));
+            const int64_t s1 = min(p1, (int64_t)boff[t] + filled);
+            if (s1 <= s0) continue;  // uniform over the block
+            const int64_t b0 = (int64_t)t * p.tile;
+            const int n = (int)min((int64_t)p.tile, PA - b0);
+            for (int i = 4 * tid; i < n; i += 4 * kThreads) {
+                if (i + 3 < n) {
+                    *reinterpret_cast<float4*>(vt + i) = __ldcg(reinterpret_cast<const float4*>(vg + b0 + i));
+                } else {
+                    for (int z = i; z < n; ++z) vt[z] = __ldcg(vg + b0 + z);
+                }
+            }
+            __syncthreads();
+            const TableEntry e = table[t];
+            for (int64_t k = s0 + tid; k < s1; k += kThreads) {
+                const int2 d = __ldcg(p.bins + k);
+                float uh, ul, th2, tl2, xh, xl;
+                u32_pair((uint32_t)d.y, uh, ul);
+                draw_target(uh, ul, Wh, Wl, th2, tl2);
+                local_target(e, th2, tl2, xh, xl);
+                p.anc[d.x] = (int32_t)(b0 + search_tile<false>(vt, n, e.il, xh, xl) - p.lead);
+            }
+            __syncthreads();  // vt is reloaded for the next tile
+        }
+    }
+    if (p.trace) {
+        __syncthreads();
+        trace_stamp(p.trace, p.trace_cap, cta, 4);
+    }
+}
+
+template <int KK>
+static cudaError_t launch_mb(const SortedParams& p, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = multinomial_binned_smem(p.n_tiles, p.tile);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_multinomial_binned<KK>, p);
+}
+
+cudaError_t launch_multinomial_binned(const SortedParams& p, int grid, cudaStream_t s) {
+    const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
+    if (p.n_tiles < 1 || p.n_tiles > kMaxTilesTotal || R > kMaxOwn || (int64_t)grid * R < p.n_tiles ||
+        p.tile < 4 || p.tile > kTileMax || grid > kThreads || !p.bins || !p.cursors || !p.v_out)
+        return cudaErrorInvalidValue;
+    const int q = (p.tile + kThreads - 1) / kThreads;
+    if (q <= 4) return launch_mb<4>(p, grid, s);
+    if (q <= 8) return launch_mb<8>(p, grid, s);
+    return launch_mb<16>(p, grid, s);
+}
+
+// Resident CTAs per SM of the binned kernel at `smem` bytes (the smallest
+// over the three widths); raises their shared-memory limits on the way.
+int multinomial_binned_blocks_per_sm(size_t smem) {
+    int best = 1 << 30;
+    cudaError_t e = cudaSuccess;
+    auto one = [&](auto kern) {
+        int nb = 0;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)multinomial_binned_smem(kMaxTilesTotal, kTileMax));
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem);
+        best = min(best, nb);
+    };
+    one(k_multinomial_binned<4>);
+    one(k_multinomial_binned<8>);
+    one(k_multinomial_binned<16>);
+    return e == cudaSuccess ? best : 0;
 }
 
 template <int KIND, int KK>

@@ -86,20 +86,16 @@ __device__ __forceinline__ TileSummary tile_scan_k(const float* __restrict__ bas
     float* x = th.v;
     tile_load_k<KK>(base, lo, n, e0, th.v);
 
-    // 1. tile maximum and domain check
+    // 1. tile maximum and domain check: the thread's maximum propagates NaN, so
+    // one test of it finds a NaN or +inf element
     float m = -INFINITY;
-    int bad = 0;
 #pragma unroll
-    for (int i = 0; i < KK; ++i) {
-        bad |= !(x[i] <= 3.402823466e38f);  // NaN or +inf
-        m = fmaxf(m, x[i]);
-    }
-    m = warp_max(m);
+    for (int i = 0; i < KK; ++i) m = fmax_nan(m, x[i]);
+    int bad = !(m <= 3.402823466e38f);
+    m = warp_max_redux(m);
     if (lane == 0) sm.redf[warp] = m;
     bad = __syncthreads_or(bad);
-    float mt = sm.redf[0];
-#pragma unroll
-    for (int w = 1; w < kWarps; ++w) mt = fmaxf(mt, sm.redf[w]);
+    const float mt = warp_max_redux(lane < kWarps ? sm.redf[lane] : -INFINITY);
     const int k = tile_exponent(mt);
     const fpair R = tile_reference(k);
 
@@ -133,15 +129,18 @@ __device__ __forceinline__ TileSummary tile_scan_k(const float* __restrict__ bas
         if (lane >= o) inc += h;
     }
     if (lane == 31) sm.wtot[warp] = inc;
-    if (p >= 0) atomicMax(&sm.i_last, e0 + p);
+    const int il = __reduce_max_sync(0xffffffffu, p >= 0 ? e0 + p : -1);
+    if (lane == 0 && il >= 0) atomicMax(&sm.i_last, il);
     __syncthreads();
-    long long wbase = 0, total = 0;
+    // every warp scans the kWarps warp totals (lane w holds warp w's)
+    long long ws = lane < kWarps ? sm.wtot[lane] : 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        const long long x = sm.wtot[w];
-        wbase += (w < warp) ? x : 0;
-        total += x;
+    for (int o = 1; o < kWarps; o <<= 1) {
+        const long long h = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += h;
     }
+    const long long total = __shfl_sync(0xffffffffu, ws, kWarps - 1);
+    const long long wbase = warp > 0 ? __shfl_sync(0xffffffffu, ws, warp - 1) : 0;
     const long long excl = wbase + inc - tot;
     const float Vk = (float)excl * 0x1p-48f, Vn = (float)(excl + tot) * 0x1p-48f;
     const float S_hi = (float)total;

@@ -49,6 +49,7 @@ SIGNATURES = {
     "pf_set_min_tile": (_INT, [_INT, _I64, _INT]),
     "pf_get_min_tile": (_INT, [_INT, _I64]),
     "pf_resample_batched_masked": (_INT, [_INT, _VP, _VP, _INT, _INT, _VP, _VP, _VP, _VP]),
+    "pf_resample_batched_metropolis_bound": (_INT, [_VP, _VP, _INT, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
     "pf_lg_init": (_INT, [_INT, _I64, _INT, ctypes.c_float, ctypes.c_float, _U64, _VP, _VP, _VP, _VP, _VP, _VP,
                           _VP]),
     "pf_lg_step": (_INT, [_INT, _I64, _INT, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _INT, _U64,
@@ -134,6 +135,13 @@ def pf_ess(logw, P, ess_out, log_sum_out=None, stream=None):
 def pf_resample_batched(kind, logw, offsets, F, B, seeds, ancestors, stream=None):
     _check(load().pf_resample_batched(kind, _ptr(logw), _ptr(offsets), F, B, _ptr(seeds), _ptr(ancestors),
                                       _stream(stream)), "pf_resample_batched")
+
+
+def pf_resample_batched_metropolis_bound(logw, offsets, F, eps, seeds, ancestors, B_out=None, mask=None,
+                                         stream=None):
+    _check(load().pf_resample_batched_metropolis_bound(_ptr(logw), _ptr(offsets), F, float(eps), _ptr(seeds),
+                                                       _ptr(mask), _ptr(ancestors), _ptr(B_out), _stream(stream)),
+           "pf_resample_batched_metropolis_bound")
 
 
 def pf_resample_batched_masked(kind, logw, offsets, F, B, seeds, mask, ancestors, stream=None):

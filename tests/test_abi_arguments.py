@@ -68,7 +68,10 @@ CHILD = textwrap.dedent(r"""
         add("pf_resample_batched_masked", k, A, B_, 4, 0, B_ + 4096, B_ + 2, B_ + 8192, None)  # mask misaligned
     add("pf_resample_batched", -1, A, B_, 4, 0, B_ + 4096, B_ + 8192, None)            # bad kind
     add("pf_resample_batched", 4, A, B_, 4, 0, B_ + 4096, B_ + 8192, None)
-    add("pf_resample_batched", pf.PF_METROPOLIS, A, B_, 4, -1, B_ + 4096, B_ + 8192, None)   # B < 0
+    add("pf_resample_batched_metropolis_bound", A, B_, 4, 0.0, B_ + 4096, None, B_ + 8192, None, None)  # eps = 0
+    add("pf_resample_batched_metropolis_bound", A, B_, 4, 1.0, B_ + 4096, None, B_ + 8192, None, None)  # eps = 1
+    add("pf_resample_batched_metropolis_bound", A, B_, 4, 0.01, B_ + 4096, None, B_ + 8192, B_ + 2, None)  # B_out
+    add("pf_resample_batched_metropolis_bound", A, B_, 0, 0.01, B_ + 4096, None, B_ + 8192, None, None)  # F = 0
 
     add("pf_reserve", -1, 0, 0, None)
     add("pf_reserve", 0, -1, 0, None)

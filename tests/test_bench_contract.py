@@ -4,14 +4,17 @@ import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
                         "--warmup", "3", "--P", "65536"], capture_output=True, text=True, timeout=600,
                        env=dict(os.environ, RANK="0", WORLD_SIZE="1"))
+    wall = time.perf_counter() - t0
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -23,3 +26,7 @@ def test_reference_arm_json_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert "workload" in d["config"]
+    # the step time is measured on the sample that ran, so the timed steps fit inside the run
+    assert d["ms_per_step"] * d["steps"] / 1e3 <= d["cpu_baseline"]["seconds_measured"] * 1.01 + 1e-3
+    assert d["cpu_baseline"]["seconds_measured"] <= wall
+    assert d["ms_per_step_full_P_estimate"] >= d["ms_per_step"]

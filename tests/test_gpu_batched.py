@@ -154,3 +154,49 @@ def test_split_filter_timeout_is_reported_and_recovered():
         rep = check_cumulative("systematic", l, a[off[f]:off[f + 1]], oracle.systematic(l, int(seeds[f]), f),
                                int(seeds[f]), filter_id=f)
         assert rep.ok, (f, rep.summary())
+
+
+def test_batched_metropolis_takes_each_filters_own_bound():
+    # B < 0: every filter takes B from Eq. 5 with its own largest normalised weight.
+    # The B the device chose equals the host bound of the FP64 w_max (one step off at
+    # most, and only where the bound sits at an integer), and each filter's chains equal
+    # the oracle's for that B; the plain batched call with B = -1 is the same call at
+    # eps = 0.01.  Filters staged in shared memory and larger ones (read from L2), a
+    # one-particle filter, an all-equal filter (w_max = 1/P, so lambda = 0 and B = 1)
+    # and an empty one.
+    sizes = [3000, 1, 777, 0, 20000, 57344, 57345, 70001, 12, 4096]
+    spreads = [1.0, 0.5, 2.0, 1.0, 0.7, 1.2, 1.2, 0.9, 3.0, 0.0]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    lw = workloads.batched_logw(off, np.array(spreads), seed=5)
+    seeds = workloads.batched_seeds(len(sizes), base=900)
+    F = len(sizes)
+    d_lw = torch.from_numpy(lw).cuda()
+    d_off = torch.from_numpy(off).cuda()
+    d_seeds = torch.from_numpy(seeds.view(np.int64)).cuda()
+    for eps in (0.01, 0.1):
+        anc = torch.full((lw.size,), -9, dtype=torch.int32, device="cuda")
+        B_out = torch.full((F,), -5, dtype=torch.int32, device="cuda")
+        pf.pf_resample_batched_metropolis_bound(d_lw, d_off, F, eps, d_seeds, anc, B_out)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        a, Bg = anc.cpu().numpy(), B_out.cpu().numpy()
+        off_by_one = 0
+        for f in range(F):
+            lo, hi = off[f], off[f + 1]
+            if hi == lo:
+                assert Bg[f] == -5  # skipped: left untouched
+                continue
+            l = lw[lo:hi]
+            w = np.exp(l.astype(np.float64) - l.max())
+            B_host = pf.pf_metropolis_B(hi - lo, w.max() / w.sum(), eps)
+            assert abs(int(Bg[f]) - B_host) <= 1, (f, Bg[f], B_host)
+            off_by_one += int(Bg[f]) != B_host
+            rep = check_metropolis(l, int(Bg[f]), a[lo:hi], oracle.metropolis(l, int(Bg[f]), int(seeds[f]), f),
+                                   int(seeds[f]), filter_id=f)
+            assert rep.ok, (f, rep.summary())
+        assert off_by_one <= 1
+        print(f"\neps={eps}: per-filter B {Bg.tolist()}")
+        if eps == 0.01:
+            anc2 = torch.full((lw.size,), -9, dtype=torch.int32, device="cuda")
+            pf.pf_resample_batched(pf.PF_METROPOLIS, d_lw, d_off, F, -1, d_seeds, anc2)
+            assert pf.pf_get_device_status() == pf.PF_OK
+            assert torch.equal(anc, anc2)
