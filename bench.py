@@ -344,6 +344,15 @@ def run_gpu(args):
     headline = breakdown["systematic"]
 
     e2e = run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes) if not args.no_e2e else None
+    figure2 = None
+    if not args.no_figure2:  # the paper's experiment at P = 2^16, compact
+        f2 = run_figure2(args, pf, torch, dev, Ps=[1 << 16], R=200)
+        figure2 = {"workload": f2["workload"],
+                   "by_alpha": {str(r["alpha"]): {"ess_over_P": r["ess_over_P"], "metropolis_B": r["metropolis_B"],
+                                                  **{k: {"us": r[k]["us"], "error": r[k]["error"]}
+                                                     for k in ("multinomial", "stratified", "systematic",
+                                                               "metropolis")}}
+                                for r in f2["rows"]}}
     batched = run_batched_compare(args, pf, torch, dev, stream, hbm_peak) if not args.no_batched else None
     bootstrap = run_bootstrap(args, pf, torch, dev, hbm_peak) if not args.no_bootstrap else None
 
@@ -381,6 +390,7 @@ def run_gpu(args):
         "e2e": e2e,
         "batched": batched,
         "bootstrap": bootstrap,
+        "figure2": figure2,
         "clocks": clocks,
         "wall_s": round(wall, 3),
     }
@@ -581,6 +591,28 @@ def run_batched_compare(args, pf, torch, dev, stream, hbm_peak):
                          "ratio": round(ms_pf / ms, 2), "ratio_vs_graph": round(ms_graph / ms, 2),
                          "achieved_gbs": round(8 * total / (ms * 1e-3) / 1e9, 1),
                          "hbm_frac": round(8 * total / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    # Metropolis B = 32 on the opt-in seven-round Philox stream (same work, fewer rounds per step)
+    pf.pf_set_metropolis_philox_rounds(7)
+    try:
+        pf.pf_resample_batched(pf.PF_METROPOLIS, lw, d_off, F, METRO_B, seeds, anc, stream)
+        torch.cuda.synchronize(dev)
+        ms7 = 0.0
+        for r in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pf.pf_resample_batched(pf.PF_METROPOLIS, lw, d_off, F, METRO_B, seeds, anc, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms7 += e0.elapsed_time(e1)
+        ms7 /= reps
+    finally:
+        pf.pf_set_metropolis_philox_rounds(10)
+    steps_total = total * METRO_B
+    by_kind["metropolis_philox7"] = {"batched_ms": round(ms7, 4), "chain_steps_per_s": round(steps_total / (ms7 * 1e-3), 1),
+                                     "philox10_chain_steps_per_s":
+                                         round(steps_total / (by_kind["metropolis"]["batched_ms"] * 1e-3), 1),
+                                     "speedup_vs_philox10": round(by_kind["metropolis"]["batched_ms"] / ms7, 3)}
     # Metropolis with each filter's own B from Eq. 5 (eps = 0.01): the B range and the rate
     B_out = torch.zeros(F, dtype=torch.int32, device=dev)
     pf.pf_resample_batched_metropolis_bound(lw, d_off, F, 0.01, seeds, anc, B_out, None, stream)
@@ -711,7 +743,7 @@ def run_bootstrap(args, pf, torch, dev, hbm_peak):
             "l2": "inputs (256 MiB of states per buffer) larger than L2"}
 
 
-def run_figure2(args, pf, torch, dev):
+def run_figure2(args, pf, torch, dev, Ps=None, R=1000):
     """The paper's experiment (Section 3, Figure 2) on this GPU: symmetric
     Dirichlet(alpha) weights, alpha in {10, 1, .1, .01}, P = 256 ... 65536;
     for each resampler the mean error sum_i (o_i/P - w_i/W)^2 over 1000
@@ -728,10 +760,9 @@ def run_figure2(args, pf, torch, dev):
              "stratified": (pf.PF_STRATIFIED, pf.pf_resample_stratified),
              "systematic": (pf.PF_SYSTEMATIC, pf.pf_resample_systematic),
              "metropolis": (pf.PF_METROPOLIS, pf.pf_resample_metropolis)}
-    R = 1000
     rows = []
     alphas = [10.0, 1.0, 0.1, 0.01]
-    Ps = [1 << k for k in range(8, 17)]
+    Ps = Ps or [1 << k for k in range(8, 17)]
     for ai, alpha in enumerate(alphas):
         for P in Ps:
             lw_h = workloads.dirichlet_logw(P, alpha, seed=1000 * ai + P)
@@ -772,8 +803,9 @@ def run_figure2(args, pf, torch, dev):
                 row[name] = {"us": round(us, 2), "error": float(err.mean()), "resamplings": r}
                 del lw_r, anc, fil, o, err
             rows.append(row)
-    return {"workload": "symmetric Dirichlet(alpha) weights, alpha in {10,1,.1,.01}, P = 2^8..2^16; "
-                        "error = mean over resamplings of sum_i (o_i/P - w_i/W)^2; runtime = median single call",
+    return {"workload": "symmetric Dirichlet(alpha) weights, alpha in {10,1,.1,.01}, P = "
+                        + ", ".join(f"2^{P.bit_length() - 1}" for P in Ps)
+                        + f"; error = mean over {R} resamplings of sum_i (o_i/P - w_i/W)^2; runtime = median single call",
             "rows": rows}
 
 
@@ -1222,6 +1254,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-bootstrap", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-figure2", action="store_true")
     ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace", "sweep", "sorted",
                                        "phases"],
                     default=None,

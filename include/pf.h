@@ -38,6 +38,9 @@
  *    element stream is word j%4 of counter (j/4, 0, filter, tag).  Metropolis
  *    chain i, steps b and b+1 (b even), uses counter (i, b/2, filter, 4) whose
  *    words are (proposal_b, uniform_b, proposal_{b+1}, uniform_{b+1}).
+ *    The Metropolis chains may instead draw from Philox-4x32-7 (seven rounds
+ *    of the same function, with the same counters), a stream that costs 30%
+ *    fewer Philox rounds per step: see pf_set_metropolis_philox_rounds.
  *    Uniforms: u23(x) = (2*(x>>9)+1)*2^-24 (systematic, stratified,
  *    Metropolis), u32(x) = (2x+1)*2^-33 (multinomial); proposals
  *    j = floor(x*P/2^32).  Every call is therefore a pure function of its
@@ -337,6 +340,21 @@ int64_t pf_metropolis_B(int64_t P, double w_max, double eps);
  */
 double pf_metropolis_bias(int64_t P, double w_max, int64_t B);
 
+/*
+ * Random-number stream of the Metropolis chains (Section 3, closing
+ * paragraph: the resampler's speed hinges on the rate at which random numbers
+ * are generated).  rounds = 10 (the default) draws each chain's proposals and
+ * uniforms from Philox-4x32-10; rounds = 7 from Philox-4x32-7, the same round
+ * function stopped after seven rounds (Salmon et al., SC'11, list it among
+ * the generators that pass the Crush battery), with the same counter layout.
+ * The two settings give different, equally valid resamplings.  The setting
+ * applies to every later pf_resample_metropolis and batched Metropolis call in
+ * the process (all devices and streams).  PF_ERR_INVALID for any other value.
+ * pf_get_metropolis_philox_rounds returns the setting in effect.
+ */
+pf_status pf_set_metropolis_philox_rounds(int rounds);
+int pf_get_metropolis_philox_rounds(void);
+
 /* Human-readable name of a status code (static storage). */
 const char* pf_status_string(pf_status status);
 
@@ -396,6 +414,18 @@ pf_status pf_set_trace_buffer(uint64_t* buf, int64_t capacity);
  */
 pf_status pf_probe_l2_random_reads(const float* buf, int64_t n, int reads_per_thread, double* reads_per_second);
 
+/*
+ * Diagnostic (the arithmetic of the tile scans, Section 2's weights): the
+ * weights the cumulative resamplers and pf_ess form inside a tile whose
+ * reference exponent is k, weights[i] = exp(logw[i] - k ln 2): the
+ * subtraction of k ln 2 (held as a float pair) is error-free (TwoSum), its
+ * remainder enters to first order, and the exponential is expf.  For testing
+ * that arithmetic against an exact exp.
+ *   logw, weights  [n] float, device, 4-byte aligned;  |k| <= 2^24
+ * Asynchronous on `stream`.  PF_ERR_INVALID for bad arguments.
+ */
+pf_status pf_debug_tile_weights(const float* logw, int64_t n, int k, float* weights, void* stream);
+
 /* Largest P accepted by pf_resample_multinomial_static. */
 #define PF_STATIC_MAX_PARTICLES (1LL << 20)
 
@@ -406,11 +436,14 @@ pf_status pf_probe_l2_random_reads(const float* buf, int64_t n, int reads_per_th
  * For callers that cannot let a library allocate device memory -- code whose
  * allocator owns all device memory, real-time loops where a first-call
  * cudaMalloc (which also synchronises the device) would stall a deadline, or
- * programs that forbid allocation after start-up.  It computes exactly what
- * pf_resample_multinomial computes (same kernel, same random streams) but
- * keeps its scratch in a fixed array compiled into the library: about 4 MiB
- * of device memory (PF_STATIC_MAX_PARTICLES floats plus 16 KiB of control
- * data), present on every GPU that loads the library until the process exits.
+ * programs that forbid allocation after start-up.  It gives exactly the
+ * ancestors pf_resample_multinomial gives (same random streams, same search
+ * predicate), by the single-launch multinomial kernel with a plain binary
+ * search per draw rather than the binned draws of pf_resample_multinomial, and
+ * keeps its scratch in a fixed array compiled into the library:
+ * PF_STATIC_MAX_PARTICLES floats of cumulative weights (4 MiB) plus 256 bytes of
+ * control words and 16 KiB of tile records, present on every GPU that loads
+ * the library until the process exits.
  *   logw          [P] float, device, 16-byte aligned               (in)
  *   P             1 <= P <= PF_STATIC_MAX_PARTICLES; larger P returns
  *                 PF_ERR_INVALID without doing anything
@@ -418,15 +451,18 @@ pf_status pf_probe_l2_random_reads(const float* buf, int64_t n, int reads_per_th
  *   ancestors     [P] int32, device, 16-byte aligned               (out)
  *   device_status [1] uint32, device, or NULL: receives this call's
  *                 device-side status (0 = ok, else a pf_status code)  (out)
- * No cudaMalloc, cudaFree or other allocating call is made.  The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress)
- * and the kernel's launch limits; make that first call before capturing any
- * stream into a CUDA graph.  Every call on every stream shares the one array
- * and it keeps the previous call's contents, so calls that may overlap on the
- * GPU (different streams without ordering between them) race and give wrong
- * results: order them, or use pf_resample_multinomial, whose scratch is per
- * stream.  pf_get_device_status does not see this call's errors; use
- * device_status.
+ * No cudaMalloc, cudaFree or other allocating call is made by the library.
+ * The first call on each device is a set-up call: it looks up the array's
+ * device address (cudaGetSymbolAddress) and the kernel's launch limits, and
+ * CUDA may load the library's device code on that device then, which can
+ * allocate and synchronise inside the driver; make it at start-up, outside
+ * any deadline and before capturing any stream into a CUDA graph.  Every call
+ * on every stream shares the one array and it keeps the previous call's
+ * contents, so calls that may overlap on the GPU (different streams without
+ * ordering between them) race and give wrong results: order them, or use
+ * pf_resample_multinomial, whose scratch is per stream.  The device-side wait
+ * limit is the one pf_set_wait_limit_ns sets.  pf_get_device_status does not
+ * see this call's errors; use device_status.
  */
 pf_status pf_resample_multinomial_static(const float* logw, int64_t P, uint64_t seed, int32_t* ancestors,
                                          uint32_t* device_status, void* stream);

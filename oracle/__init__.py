@@ -63,6 +63,9 @@ def _load():
         i64, u64, u32, i32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         sig = {
             "orc_philox4x32_10": (None, [c_u32, c_u32, c_u32]),
+            "orc_philox4x32_r": (None, [c_u32, c_u32, c_u32, i32]),
+            "orc_metropolis_draws_r": (None, [u64, u32, i64, i64, i32, i32, c_i32, c_d]),
+            "orc_metropolis_chains_r": (i32, [c_f, i64, i32, u64, u32, c_i64, i64, i32, c_i32]),
             "orc_u23": (ctypes.c_double, [u32]),
             "orc_u32": (ctypes.c_double, [u32]),
             "orc_index": (u32, [u32, u32]),
@@ -130,6 +133,15 @@ def philox4x32_10(ctr, key):
     return out
 
 
+def philox4x32(ctr, key, rounds):
+    """Philox-4x32 with `rounds` rounds (the same round function)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox4x32_r(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), _p(out, ctypes.c_uint32), int(rounds))
+    return out
+
+
 def u23(x: int) -> float:
     return _load().orc_u23(int(x))
 
@@ -155,11 +167,12 @@ def stream_uniforms(seed, filter_id, tag, n, kind=0):
     return out
 
 
-def metropolis_draws(seed, filter_id, P, i, B):
+def metropolis_draws(seed, filter_id, P, i, B, rounds=10):
+    """Proposals and uniforms of chain i, steps 0..B-1 (Philox-4x32 with `rounds` rounds)."""
     prop = np.zeros(max(B, 1), dtype=np.int32)
     unif = np.zeros(max(B, 1), dtype=np.float64)
-    _load().orc_metropolis_draws(seed, filter_id, P, i, B, _p(prop, ctypes.c_int32),
-                                 _p(unif, ctypes.c_double))
+    _load().orc_metropolis_draws_r(seed, filter_id, P, i, B, int(rounds), _p(prop, ctypes.c_int32),
+                                   _p(unif, ctypes.c_double))
     return prop[:B], unif[:B]
 
 
@@ -242,18 +255,19 @@ def multinomial(lw, seed, filter_id=0):
     return a
 
 
-def metropolis(lw, B, seed, filter_id=0, chains=None):
-    """All chains, or only the chain indices in ``chains``."""
+def metropolis(lw, B, seed, filter_id=0, chains=None, rounds=10):
+    """All chains, or only the chain indices in ``chains``; draws from Philox-4x32 with
+    `rounds` rounds (10: the default stream; 7: the opt-in cheaper stream)."""
     lw = _f32(lw)
-    if chains is None:
+    if chains is None and rounds == 10:
         a = np.zeros(lw.size, dtype=np.int32)
         _check(_load().orc_metropolis(_p(lw, ctypes.c_float), lw.size, int(B), seed, filter_id,
                                       _p(a, ctypes.c_int32)))
         return a
-    idx = np.ascontiguousarray(chains, dtype=np.int64)
+    idx = np.arange(lw.size, dtype=np.int64) if chains is None else np.ascontiguousarray(chains, dtype=np.int64)
     a = np.zeros(idx.size, dtype=np.int32)
-    _check(_load().orc_metropolis_chains(_p(lw, ctypes.c_float), lw.size, int(B), seed, filter_id,
-                                         _p(idx, ctypes.c_int64), idx.size, _p(a, ctypes.c_int32)))
+    _check(_load().orc_metropolis_chains_r(_p(lw, ctypes.c_float), lw.size, int(B), seed, filter_id,
+                                           _p(idx, ctypes.c_int64), idx.size, int(rounds), _p(a, ctypes.c_int32)))
     return a
 
 

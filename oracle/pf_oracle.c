@@ -53,11 +53,13 @@ enum { TAG_SYS = 1, TAG_STRAT = 2, TAG_MULTI = 3, TAG_METRO = 4 };
 #define PHILOX_WEYL_A 0x9E3779B9u
 #define PHILOX_WEYL_B 0xBB67AE85u
 
-void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+/* The same generator with `rounds` rounds (SC'11, Table 2 lists Philox-4x32-7  */
+/* among its Crush-resistant members; 10 is the recommended default).          */
+void orc_philox4x32_r(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4], int rounds)
 {
     uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
     uint32_t k0 = key[0], k1 = key[1];
-    for (int round = 0; round < 10; ++round) {
+    for (int round = 0; round < rounds; ++round) {
         uint64_t pa = (uint64_t)PHILOX_MUL_A * x0;
         uint64_t pb = (uint64_t)PHILOX_MUL_B * x2;
         uint32_t pa_hi = (uint32_t)(pa >> 32), pa_lo = (uint32_t)pa;
@@ -71,6 +73,11 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
         k1 += PHILOX_WEYL_B;
     }
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    orc_philox4x32_r(ctr, key, out, 10);
 }
 
 static void seed_key(uint64_t seed, uint32_t key[2])
@@ -108,15 +115,16 @@ void orc_stream_uniforms(uint64_t seed, uint32_t filter, uint32_t tag, int64_t n
     }
 }
 
-/* Proposal indices and acceptance uniforms of Metropolis chain i, steps 0..B-1. */
-void orc_metropolis_draws(uint64_t seed, uint32_t filter, int64_t P, int64_t i, int B,
-                          int32_t* prop, double* unif)
+/* Proposal indices and acceptance uniforms of Metropolis chain i, steps 0..B-1, */
+/* from Philox-4x32 with `rounds` rounds (10: the library's default stream).     */
+void orc_metropolis_draws_r(uint64_t seed, uint32_t filter, int64_t P, int64_t i, int B, int rounds,
+                            int32_t* prop, double* unif)
 {
     uint32_t key[2], ctr[4], r[4];
     seed_key(seed, key);
     for (int b = 0; b < B; b += 2) {
         ctr[0] = (uint32_t)i; ctr[1] = (uint32_t)(b / 2); ctr[2] = filter; ctr[3] = TAG_METRO;
-        orc_philox4x32_10(ctr, key, r);
+        orc_philox4x32_r(ctr, key, r, rounds);
         prop[b] = (int32_t)orc_index(r[0], (uint32_t)P);
         unif[b] = orc_u23(r[1]);
         if (b + 1 < B) {
@@ -124,6 +132,12 @@ void orc_metropolis_draws(uint64_t seed, uint32_t filter, int64_t P, int64_t i, 
             unif[b + 1] = orc_u23(r[3]);
         }
     }
+}
+
+void orc_metropolis_draws(uint64_t seed, uint32_t filter, int64_t P, int64_t i, int B,
+                          int32_t* prop, double* unif)
+{
+    orc_metropolis_draws_r(seed, filter, P, i, B, 10, prop, unif);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -342,9 +356,10 @@ int orc_multinomial(const float* lw, int64_t P, uint64_t seed, uint32_t filter, 
     return st;
 }
 
-/* Metropolis chains idx[0..n) only (n = P and idx = NULL runs every chain). */
-int orc_metropolis_chains(const float* lw, int64_t P, int B, uint64_t seed, uint32_t filter,
-                          const int64_t* idx, int64_t n, int32_t* out)
+/* Metropolis chains idx[0..n) only (n = P and idx = NULL runs every chain), */
+/* their draws from Philox-4x32 with `rounds` rounds.                        */
+int orc_metropolis_chains_r(const float* lw, int64_t P, int B, uint64_t seed, uint32_t filter,
+                            const int64_t* idx, int64_t n, int rounds, int32_t* out)
 {
     if (P < 1 || B < 0) return ORC_ERR_INVALID;
     if (check_domain(lw, P)) return ORC_ERR_DOMAIN;
@@ -355,7 +370,7 @@ int orc_metropolis_chains(const float* lw, int64_t P, int B, uint64_t seed, uint
         int64_t k = i;
         for (int b = 0; b < B; b += 2) {
             ctr[0] = (uint32_t)i; ctr[1] = (uint32_t)(b / 2); ctr[2] = filter; ctr[3] = TAG_METRO;
-            orc_philox4x32_10(ctr, key, r);
+            orc_philox4x32_r(ctr, key, r, rounds);
             int64_t j = orc_index(r[0], (uint32_t)P);
             if (metropolis_accept((double)lw[j], (double)lw[k], orc_u23(r[1]))) k = j;
             if (b + 1 < B) {
@@ -366,6 +381,12 @@ int orc_metropolis_chains(const float* lw, int64_t P, int B, uint64_t seed, uint
         out[q] = (int32_t)k;
     }
     return ORC_OK;
+}
+
+int orc_metropolis_chains(const float* lw, int64_t P, int B, uint64_t seed, uint32_t filter,
+                          const int64_t* idx, int64_t n, int32_t* out)
+{
+    return orc_metropolis_chains_r(lw, P, B, seed, filter, idx, n, 10, out);
 }
 
 int orc_metropolis(const float* lw, int64_t P, int B, uint64_t seed, uint32_t filter, int32_t* anc)

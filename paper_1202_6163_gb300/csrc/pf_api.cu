@@ -17,7 +17,7 @@
 
 namespace pf {
 cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0, uint32_t key1,
-                              uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms, cudaStream_t s);
+                              uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms, cudaStream_t s, int rounds);
 cudaError_t prepare_metropolis();
 cudaError_t launch_gather(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* anc, int64_t P_dst,
                           void* dst, uint32_t* ctl, int num_sms, cudaStream_t s);
@@ -26,6 +26,7 @@ cudaError_t launch_reduce(const float* lw, int64_t P, void* rec, uint32_t* ctl, 
 int reduce_tiles(int64_t P);
 cudaError_t probe_l2_random_reads(const float* buf, int64_t n, int reads, int num_sms, double* rate);
 size_t reduce_record_bytes();
+cudaError_t launch_tile_weights(const float* lw, int64_t n, int k, float* out, cudaStream_t s);
 }  // namespace pf
 
 using namespace pf;
@@ -52,16 +53,29 @@ struct Workspace {
     size_t scratch_bytes = 0;
     uint32_t* counters = nullptr;  // per-filter arrival counters, zero between launches
     size_t n_counters = 0;
+    unsigned long long* metro = nullptr;  // batched Metropolis: two epoch-tagged words per filter
+    size_t n_metro = 0;                   // filters they cover
 };
 
 std::mutex g_mu;
 DeviceInfo g_dev[kMaxDevices];
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 uint64_t g_wait_ns = 1000000000ull;
+int g_metro_rounds = 10;  // Philox rounds of the Metropolis chains (pf_set_metropolis_philox_rounds)
 int64_t g_skip_tile = -1;
 static_assert(kTraceWords == PF_TRACE_WORDS, "trace record layout");
 uint64_t* g_trace = nullptr;  // phase-trace buffer (pf_set_trace_buffer), or null
 int64_t g_trace_cap = 0;
+
+}  // namespace
+
+// The wait limit set by pf_set_wait_limit_ns (read by the allocation-free entry point too).
+uint64_t pf::current_wait_ns() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_wait_ns;
+}
+
+namespace {
 
 pf_status cuda_fail(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return PF_OK;
@@ -155,6 +169,28 @@ pf_status ensure_counters(Workspace& w, size_t n, cudaStream_t s) {
     }
     w.counters = c;
     w.n_counters = n;
+    return PF_OK;
+}
+
+// At least n filters' batched-Metropolis words in w (allocated and zeroed on growth;
+// only the batched Metropolis kernel writes them).
+pf_status ensure_metro(Workspace& w, size_t n, cudaStream_t s) {
+    if (n <= w.n_metro) return PF_OK;
+    if (capturing(s)) return PF_ERR_NOMEM;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (w.metro) cudaFree(w.metro);
+    w.metro = nullptr;
+    w.n_metro = 0;
+    unsigned long long* m = nullptr;
+    if (cudaMalloc(&m, 2 * n * sizeof(unsigned long long)) != cudaSuccess) return PF_ERR_NOMEM;
+    e = cudaMemsetAsync(m, 0, 2 * n * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cudaFree(m);
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    w.metro = m;
+    w.n_metro = n;
     return PF_OK;
 }
 
@@ -328,8 +364,9 @@ pf_status pf_resample_metropolis(const float* logw, int64_t P, int B, uint64_t s
         if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
         B_dev = w->ctl + CTL_METRO_B;
     }
-    return cuda_fail(launch_metropolis(logw, P, B, B_dev, k0, k1, 0u, ancestors, w->ctl, info->num_sms, s),
-                     "metropolis launch");
+    return cuda_fail(
+        launch_metropolis(logw, P, B, B_dev, k0, k1, 0u, ancestors, w->ctl, info->num_sms, s, g_metro_rounds),
+        "metropolis launch");
 }
 
 pf_status pf_gather(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* ancestors, int64_t P_dst,
@@ -400,9 +437,13 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     if (st) return st;
     st = ensure_counters(*w, 2 * (size_t)F, s);
     if (st) return st;
+    if (kind == PF_METROPOLIS) {
+        st = ensure_metro(*w, (size_t)F, s);
+        if (st) return st;
+    }
     int32_t* items = reinterpret_cast<int32_t*>((char*)w->scratch + items_at);
     const int split = kind == PF_STRATIFIED || kind == PF_SYSTEMATIC;
-    cudaError_t e = launch_batched_plan(logw, offsets, F, mask, split, items, w->ctl, s);
+    cudaError_t e = launch_batched_plan(logw, offsets, F, mask, split, items, w->ctl, s, kind == PF_METROPOLIS);
     if (e != cudaSuccess) return cuda_fail(e, "batched plan launch");
     BatchParams bp;
     bp.lw = logw;
@@ -424,6 +465,8 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     bp.trace_cap = g_trace_cap;
     bp.B_out = B_out;
     bp.eps = eps;
+    bp.metro = kind == PF_METROPOLIS ? w->metro : nullptr;
+    bp.rounds = g_metro_rounds;
     if (kind == PF_METROPOLIS) return cuda_fail(launch_batched_metropolis(bp, grid, s), "batched metropolis launch");
     return cuda_fail(launch_batched(kind, bp, grid, s), "batched launch");
 }
@@ -478,6 +521,8 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     if (st) return st;
     if (F_max > 0) {
         st = ensure_counters(*w, 2 * (size_t)F_max, s);
+        if (st) return st;
+        st = ensure_metro(*w, (size_t)F_max, s);
         if (st) return st;
     }
     return cuda_fail(cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -544,6 +589,25 @@ pf_status pf_set_wait_limit_ns(uint64_t ns) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_wait_ns = ns;
     return PF_OK;
+}
+
+pf_status pf_debug_tile_weights(const float* logw, int64_t n, int k, float* weights, void* stream) {
+    if (!logw || !weights || n < 1 || k < -(1 << 24) || k > (1 << 24) || ((uintptr_t)logw & 3u) ||
+        ((uintptr_t)weights & 3u))
+        return PF_ERR_INVALID;
+    return cuda_fail(launch_tile_weights(logw, n, k, weights, (cudaStream_t)stream), "tile weights launch");
+}
+
+pf_status pf_set_metropolis_philox_rounds(int rounds) {
+    if (rounds != 10 && rounds != 7) return PF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_metro_rounds = rounds;
+    return PF_OK;
+}
+
+int pf_get_metropolis_philox_rounds(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_metro_rounds;
 }
 
 pf_status pf_set_trace_buffer(uint64_t* buf, int64_t capacity) {

@@ -339,10 +339,18 @@ constexpr int kPlanThreads = 1024;
 __global__ void __launch_bounds__(kPlanThreads) k_batched_plan(const float* __restrict__ lw,
                                                                const int64_t* __restrict__ offsets, int F,
                                                                const int32_t* __restrict__ mask, int split,
-                                                               int32_t* __restrict__ items, uint32_t* ctl) {
+                                                               int32_t* __restrict__ items, uint32_t* ctl, int metro) {
     __shared__ int count[kMaxOwnB + 1], start[kMaxOwnB + 1];
     const int tid = threadIdx.x;
     if (tid <= kMaxOwnB) count[tid] = 0;
+    if (metro) {
+        // Metropolis: a new launch epoch, and an empty list of shared filters after the items
+        if (tid == 0) {
+            ctl[CTL_METRO_EPOCH] += 1u;
+            ctl[CTL_HEAVY] = 0u;
+        }
+        for (int i = tid; i < min(F, kMaxHeavy); i += kPlanThreads) items[F + i] = 0;
+    }
     __syncthreads();
     auto tiles = [&](int f) -> int {  // 0: no item
         if (mask && mask[f] == 0) return 0;
@@ -387,8 +395,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_batched_plan(const float* __re
 }
 
 cudaError_t launch_batched_plan(const float* lw, const int64_t* offsets, int F, const int32_t* mask, int split,
-                                int32_t* items, uint32_t* ctl, cudaStream_t s) {
-    k_batched_plan<<<1, kPlanThreads, 0, s>>>(lw, offsets, F, mask, split, items, ctl);
+                                int32_t* items, uint32_t* ctl, cudaStream_t s, int metro) {
+    k_batched_plan<<<1, kPlanThreads, 0, s>>>(lw, offsets, F, mask, split, items, ctl, metro);
     return cudaGetLastError();
 }
 

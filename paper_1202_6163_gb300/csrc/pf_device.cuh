@@ -21,10 +21,13 @@ struct u32x4 {
     uint32_t x, y, z, w;
 };
 
+// ROUNDS rounds of the same function: 10 is the default stream; 7 (listed in
+// SC'11 among the Crush-resistant members) is the opt-in cheaper Metropolis stream.
+template <int ROUNDS = 10>
 __device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                         uint32_t k0, uint32_t k1) {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = 0; r < ROUNDS; ++r) {
         // one 32x32->64 product each (both halves used)
         const uint64_t a = (uint64_t)0xD2511F53u * c0;
         const uint64_t b = (uint64_t)0xCD9E8D57u * c2;
@@ -104,14 +107,16 @@ __device__ __forceinline__ fpair tile_reference(int k) {
     return {hi, __fmaf_rn(kf, kLn2Lo, err)};
 }
 
-// exp(lw - R) with R = (R.hi, R.lo): the subtraction is error-free, the
-// residual enters as a first-order factor.  Zero for lw = -inf.
+// exp(lw - R) with R = (R.hi, R.lo): the subtraction is error-free and the
+// residual d enters as the factor 1 + d + d^2/2 (for a reference k ln 2 beyond
+// ~2^16 in magnitude, R.lo, and so d, reaches 4e-3, where the first-order
+// factor alone would leave an error d^2/2 near 8e-6).  Zero for lw = -inf.
 __device__ __forceinline__ float weight_rel(float lw, fpair R) {
     float s, e;
     two_sum(lw, -R.hi, s, e);
     const float d_lo = __fsub_rn(e, R.lo);
     const float x = expf(s);
-    return x > 0.f ? __fmaf_rn(x, d_lo, x) : 0.f;
+    return x > 0.f ? __fmaf_rn(x, __fmaf_rn(d_lo, 0.5f * d_lo, d_lo), x) : 0.f;
 }
 
 // ---------------------------------------------------------------------------

@@ -26,11 +26,11 @@ enum : int {
     CTL_QUEUE = 4,        // work-queue ticket of the batched kernels
     CTL_QUEUE_DONE = 5,   // completion counter of the batched kernels
     CTL_METRO_B = 6,      // Metropolis step count chosen on the device
+    CTL_METRO_EPOCH = 7,  // launch epoch of the batched Metropolis (tags its per-filter words)
     CTL_ARRIVE0 = 8,      // arrival counters of the single-launch kernels,
     CTL_ARRIVE1 = 9,      //   used by alternate epochs (one is reset while the other counts)
     CTL_ITEMS = 10,       // work items of the current batched call (written by its plan pass)
-    CTL_ARRIVE2_0 = 11,   // arrival counters of a second grid-wide wait in one launch (binned
-    CTL_ARRIVE2_1 = 12,   //   multinomial draws), alternating by epoch like CTL_ARRIVE0/1
+    CTL_HEAVY = 11,       // batched Metropolis: filters on the list of shared (heavy) filters
     CTL_WORDS = 16
 };
 
@@ -62,16 +62,14 @@ struct SortedParams {
     uint64_t* slots;  // one 16-byte record per tile
     uint64_t wait_ns;
     int skip_tile;
-    float* v_out;     // multinomial: tile-local cumulative weights (P + lead floats), else null
+    float* v_out;     // tile-local cumulative weights (P + lead floats): multinomial, and the tiles
+                      // pass 2 reloads (systematic / stratified with several tiles per CTA), else null
     int lead;         // elements of the aligned window before element 0 (0..3)
     float* c2_out;    // multinomial: every 16th |v| of each tile (cpt2 per tile), or null
     float* c1_out;    // multinomial: every 2^c1shift-th |v| of each tile (cpt1 per tile)
     int cpt2, cpt1, c1shift;
     uint64_t* trace;     // phase records (kTraceWords words each), or null
     int64_t trace_cap;   // records the trace buffer holds
-    int2* bins;          // multinomial, binned draws: bin_cap (draw, Philox word) entries, else null
-    uint32_t* cursors;   // multinomial, binned draws: one fill counter per tile
-    int64_t bin_cap;
 };
 
 // Batched call: F filters, filter f owns lw[offsets[f] .. offsets[f+1]).
@@ -94,6 +92,9 @@ struct BatchParams {
     int64_t trace_cap;
     int32_t* B_out;      // Metropolis with B < 0: each filter's chosen step count, or null
     double eps;          // Metropolis with B < 0: the eps of Eq. 4
+    unsigned long long* metro;  // Metropolis: two epoch-tagged words per filter (chain-block claims,
+                                // published step count), in a buffer no other kernel writes
+    int rounds;                 // Metropolis: Philox rounds of the chains' stream (10 or 7)
 };
 
 // Phase record of a traced CTA or work item: global-timer stamps at the start,
@@ -142,15 +143,11 @@ struct LgParams {
     uint32_t* status;
 };
 
+// The limit of device-side waits set by pf_set_wait_limit_ns (host).
+uint64_t current_wait_ns();
+
 // Kernel launchers (defined in the .cu files; return the launch error).
 cudaError_t launch_sorted_persistent(int kind, const SortedParams& p, int grid, cudaStream_t s);
-// Binned multinomial draws: shared memory of a launch with T tiles of `tile`
-// log-weights, the resident CTAs per SM at that size, the launch, and the bin
-// capacity the kernel needs at most.
-size_t multinomial_binned_smem(int T, int tile);
-int multinomial_binned_blocks_per_sm(size_t smem);
-cudaError_t launch_multinomial_binned(const SortedParams& p, int grid, cudaStream_t s);
-int64_t multinomial_bin_cap(int64_t P, int T);
 int lg_tile();
 cudaError_t launch_lg_init(const LgParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_lg_step(const LgParams& p, cudaStream_t s);
@@ -162,7 +159,8 @@ cudaError_t launch_gather_inplace(void* x, int64_t P, int64_t row_bytes, const i
 int persistent_blocks_per_sm(int kind);
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s);
 cudaError_t launch_batched_plan(const float* lw, const int64_t* offsets, int F, const int32_t* mask, int split,
-                                int32_t* items, uint32_t* ctl, cudaStream_t s);
+                                int32_t* items, uint32_t* ctl, cudaStream_t s, int metro = 0);
+constexpr int kMaxHeavy = 4096;  // batched Metropolis: length of the list of shared filters
 constexpr int kMaxItemsPerFilter = 16;  // tiles of a batched filter (kMaxOwnB)
 int batched_blocks_per_sm(int kind);
 size_t batched_scratch_floats_per_cta();

@@ -37,6 +37,7 @@ __device__ __forceinline__ bool metropolis_accept(float lj, float lk, float u) {
 // issues all their log-weight loads before resolving the steps in order.
 constexpr int kAhead = 4;
 
+template <int ROUNDS>
 __device__ __forceinline__ void run_chain(const float* __restrict__ lw, uint32_t Pu, uint32_t i, int steps,
                                           uint32_t filter, uint32_t key0, uint32_t key1, uint32_t& k, float& lk) {
     for (int b0 = 0; b0 < steps; b0 += kAhead) {
@@ -44,7 +45,7 @@ __device__ __forceinline__ void run_chain(const float* __restrict__ lw, uint32_t
         float uu[kAhead], ll[kAhead];
 #pragma unroll
         for (int q = 0; q < kAhead / 2; ++q) {
-            const u32x4 r = philox(i, (uint32_t)((b0 >> 1) + q), filter, TAG_METRO, key0, key1);
+            const u32x4 r = philox<ROUNDS>(i, (uint32_t)((b0 >> 1) + q), filter, TAG_METRO, key0, key1);
             jj[2 * q] = draw_index(r.x, Pu);
             uu[2 * q] = u23f(r.y);
             jj[2 * q + 1] = draw_index(r.z, Pu);
@@ -65,6 +66,7 @@ __device__ __forceinline__ void run_chain(const float* __restrict__ lw, uint32_t
 // B steps of chain i from state k over staged weights w (shared memory).
 constexpr float kWeightFloor = 0x1p-100f;
 
+template <int ROUNDS>
 __device__ __forceinline__ void run_chain_w(const float* __restrict__ lw, const float* w, uint32_t Pu, uint32_t i,
                                             int steps, uint32_t filter, uint32_t key0, uint32_t key1, uint32_t& k) {
     float wk = w[k];
@@ -73,7 +75,7 @@ __device__ __forceinline__ void run_chain_w(const float* __restrict__ lw, const 
         float uu[kAhead], ww[kAhead];
 #pragma unroll
         for (int q = 0; q < kAhead / 2; ++q) {
-            const u32x4 r = philox(i, (uint32_t)((b0 >> 1) + q), filter, TAG_METRO, key0, key1);
+            const u32x4 r = philox<ROUNDS>(i, (uint32_t)((b0 >> 1) + q), filter, TAG_METRO, key0, key1);
             jj[2 * q] = draw_index(r.x, Pu);
             uu[2 * q] = u23f(r.y);
             jj[2 * q + 1] = draw_index(r.z, Pu);
@@ -208,7 +210,7 @@ __device__ uint32_t bound_B(int64_t P, double w_max, double eps, uint32_t cap) {
     return b < (double)cap ? (uint32_t)b : cap;
 }
 
-template <bool STAGED>
+template <bool STAGED, int ROUNDS>
 __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __restrict__ lw, int64_t P, int B,
                                                               const uint32_t* __restrict__ B_dev, uint32_t key0,
                                                               uint32_t key1, uint32_t filter,
@@ -221,11 +223,11 @@ __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __res
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t k = (uint32_t)i;
         if (STAGED) {
-            run_chain_w(lw, wsm, Pu, (uint32_t)i, steps, filter, key0, key1, k);
+            run_chain_w<ROUNDS>(lw, wsm, Pu, (uint32_t)i, steps, filter, key0, key1, k);
         } else {
             float lk = __ldg(lw + i);
             if (!(lk <= 3.402823466e38f)) set_status(ctl + CTL_STATUS, ST_DOMAIN);  // NaN or +inf
-            run_chain(lw, Pu, (uint32_t)i, steps, filter, key0, key1, k, lk);
+            run_chain<ROUNDS>(lw, Pu, (uint32_t)i, steps, filter, key0, key1, k, lk);
         }
         anc[i] = (int32_t)k;
     }
@@ -233,28 +235,42 @@ __global__ void __launch_bounds__(kMetroThreads) k_metropolis(const float* __res
 
 // Once per device: allow the staged variant its full shared-memory copy.
 cudaError_t prepare_metropolis() {
-    return cudaFuncSetAttribute(k_metropolis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kMetroSmemFloats * (int)sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(k_metropolis<true, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMetroSmemFloats * (int)sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_metropolis<true, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMetroSmemFloats * (int)sizeof(float));
+    return e;
 }
 
-cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0, uint32_t key1,
-                              uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms, cudaStream_t s) {
+template <int ROUNDS>
+static cudaError_t launch_metropolis_r(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0,
+                                       uint32_t key1, uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms,
+                                       cudaStream_t s) {
     const bool staged = P <= kMetroSmemFloats;
     const int64_t blocks_needed = (P + kMetroThreads - 1) / kMetroThreads;
     if (staged) {
         // every CTA stages the full vector, so keep the grid to what runs at once
         const size_t smem = (size_t)P * sizeof(float);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_metropolis<true>, kMetroThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_metropolis<true, ROUNDS>, kMetroThreads, smem);
         if (per_sm < 1) per_sm = 1;
         const int64_t grid = blocks_needed < (int64_t)num_sms * per_sm ? blocks_needed : (int64_t)num_sms * per_sm;
-        k_metropolis<true><<<(unsigned)grid, kMetroThreads, smem, s>>>(lw, P, B, B_dev, key0, key1, filter, anc, ctl);
+        k_metropolis<true, ROUNDS><<<(unsigned)grid, kMetroThreads, smem, s>>>(lw, P, B, B_dev, key0, key1, filter,
+                                                                               anc, ctl);
     } else {
         const int64_t cap = (int64_t)num_sms * 64;
         const int64_t grid = blocks_needed < cap ? blocks_needed : cap;
-        k_metropolis<false><<<(unsigned)grid, kMetroThreads, 0, s>>>(lw, P, B, B_dev, key0, key1, filter, anc, ctl);
+        k_metropolis<false, ROUNDS><<<(unsigned)grid, kMetroThreads, 0, s>>>(lw, P, B, B_dev, key0, key1, filter,
+                                                                             anc, ctl);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0, uint32_t key1,
+                              uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms, cudaStream_t s, int rounds) {
+    if (rounds == 7) return launch_metropolis_r<7>(lw, P, B, B_dev, key0, key1, filter, anc, ctl, num_sms, s);
+    return launch_metropolis_r<10>(lw, P, B, B_dev, key0, key1, filter, anc, ctl, num_sms, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -269,12 +285,66 @@ constexpr int kMetroBThreads = 1024;
 constexpr int kMetroBStage = 56 * 1024;  // floats staged per CTA (224 KiB)
 constexpr uint32_t kBatchedBCap = 1u << 24;  // largest step count chosen for B < 0
 
+// Chain blocks of a filter shared by several CTAs: a filter whose chains
+// number more than one block and whose work P_f B_f reaches kHeavyWork steps
+// is put on a list after its owner (the CTA that took its ticket) has
+// published its step count; CTAs that find the ticket queue empty join the
+// listed filters.  Blocks of kMetroBThreads chains are claimed through a 64-bit
+// word per filter, (launch epoch, claims): a word from an earlier launch is
+// replaced by the first claimer, so no pass clears the words between launches.
+// Every chain depends only on (f, i, B_f), so which CTA runs it does not
+// change the result.
+constexpr long long kHeavyWork = 1LL << 22;
+
+// Claims the next block of the filter's word (thread 0 only).
+__device__ __forceinline__ uint32_t claim_block(unsigned long long* w, uint32_t epoch) {
+    for (;;) {
+        const unsigned long long old = (unsigned long long)ld_relaxed_u64(reinterpret_cast<const uint64_t*>(w));
+        if ((uint32_t)(old >> 32) != epoch) {
+            if (atomicCAS(w, old, ((unsigned long long)epoch << 32) | 1ull) == old) return 0u;
+            continue;
+        }
+        return (uint32_t)atomicAdd(w, 1ull);
+    }
+}
+
+// The chains of blocks claimed from filter f (block-wide; the weights are staged).
+template <int ROUNDS>
+__device__ __forceinline__ void run_claimed_blocks(const BatchParams& bp, const float* lw, const float* wsm, bool staged,
+                                                   int64_t Pf, int64_t off0, int steps, int f, uint32_t epoch,
+                                                   uint32_t key0, uint32_t key1, int* blk_sm) {
+    const int tid = threadIdx.x;
+    const uint32_t Pu = (uint32_t)Pf;
+    const int64_t nblk = (Pf + kMetroBThreads - 1) / kMetroBThreads;
+    for (;;) {
+        if (tid == 0) *blk_sm = (int)claim_block(bp.metro + 2 * (int64_t)f, epoch);
+        __syncthreads();
+        const int64_t blk = *blk_sm;
+        __syncthreads();
+        if (blk >= nblk) break;
+        const int64_t i = blk * kMetroBThreads + tid;
+        if (i < Pf) {
+            uint32_t k = (uint32_t)i;
+            if (staged) {
+                run_chain_w<ROUNDS>(lw, wsm, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k);
+            } else {
+                float lk = __ldg(lw + i);
+                if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
+                run_chain<ROUNDS>(lw, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k, lk);
+            }
+            bp.anc[off0 + i] = (int32_t)k;
+        }
+    }
+}
+
+template <int ROUNDS>
 __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchParams bp) {
     extern __shared__ float wsm[];
-    __shared__ int f_sm, f_B;
+    __shared__ int f_sm, f_B, blk_sm;
     __shared__ float red[kMetroBThreads / 32];
     const int tid = threadIdx.x;
     const int n_items = (int)ld_relaxed_u32(bp.ctl + CTL_ITEMS);
+    const uint32_t epoch = ld_relaxed_u32(bp.ctl + CTL_METRO_EPOCH);
     for (;;) {
         if (tid == 0) f_sm = (int)atomicAdd(bp.ctl + CTL_QUEUE, 1u);
         __syncthreads();
@@ -314,19 +384,79 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
         const uint64_t seed = bp.seeds[f];
         const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
         const uint32_t Pu = (uint32_t)Pf;
-        for (int64_t i = tid; i < Pf; i += kMetroBThreads) {
-            uint32_t k = (uint32_t)i;
-            if (staged) {
-                run_chain_w(lw, wsm, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k);
-            } else {
-                float lk = __ldg(lw + i);
-                if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
-                run_chain(lw, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k, lk);
+        const bool heavy = bp.metro != nullptr && Pf > kMetroBThreads && Pf * (long long)max(steps, 1) >= kHeavyWork;
+        if (heavy) {
+            // publish the step count, then list the filter for CTAs with nothing left to take
+            if (tid == 0) {
+                st_release_u64(reinterpret_cast<uint64_t*>(bp.metro + 2 * (int64_t)f + 1),
+                               ((uint64_t)epoch << 32) | (uint32_t)steps);
+                const uint32_t h = atomicAdd(bp.ctl + CTL_HEAVY, 1u);
+                if (h < (uint32_t)kMaxHeavy) {  // the list lives after the items (scratch the plan cleared)
+                    int32_t* list = const_cast<int32_t*>(bp.items) + bp.F;
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(list + h), "r"(f + 1) : "memory");
+                }
             }
-            bp.anc[off0 + i] = (int32_t)k;
+            run_claimed_blocks<ROUNDS>(bp, lw, wsm, staged, Pf, off0, steps, f, epoch, key0, key1, &blk_sm);
+        } else {
+            for (int64_t i = tid; i < Pf; i += kMetroBThreads) {
+                uint32_t k = (uint32_t)i;
+                if (staged) {
+                    run_chain_w<ROUNDS>(lw, wsm, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k);
+                } else {
+                    float lk = __ldg(lw + i);
+                    if (!(lk <= 3.402823466e38f)) set_status(bp.ctl + CTL_STATUS, ST_DOMAIN);
+                    run_chain<ROUNDS>(lw, Pu, (uint32_t)i, steps, (uint32_t)f, key0, key1, k, lk);
+                }
+                bp.anc[off0 + i] = (int32_t)k;
+            }
         }
         __syncthreads();  // the staging buffer is reused by the next filter
         trace_stamp(bp.trace, bp.trace_cap, ticket, 4);
+    }
+    // the queue is empty: join the listed filters that still have unclaimed blocks
+    if (bp.metro != nullptr) {
+        const uint64_t t_start = global_ns();
+        for (int h = 0;; ++h) {
+            if (tid == 0) {
+                const int H = (int)min(ld_acquire_u32(bp.ctl + CTL_HEAVY), (uint32_t)kMaxHeavy);
+                int f = -1;
+                if (h < H) {
+                    // the owner lists the filter right after counting it: wait (bounded) for the entry
+                    for (uint32_t it = 0;; ++it) {
+                        const uint32_t e = ld_acquire_u32(reinterpret_cast<const uint32_t*>(bp.items + bp.F + h));
+                        if (e != 0u) {
+                            f = (int)e - 1;
+                            break;
+                        }
+                        if ((it & 63u) == 63u && global_ns() - t_start > bp.wait_ns) break;
+                    }
+                }
+                f_sm = h < H ? f : -2;
+                if (f >= 0) {
+                    const uint64_t pw = ld_acquire_u64(reinterpret_cast<const uint64_t*>(bp.metro + 2 * (int64_t)f + 1));
+                    const uint64_t cw = ld_relaxed_u64(reinterpret_cast<const uint64_t*>(bp.metro + 2 * (int64_t)f));
+                    const int64_t nblk = (bp.offsets[f + 1] - bp.offsets[f] + kMetroBThreads - 1) / kMetroBThreads;
+                    const bool done = (uint32_t)(cw >> 32) == epoch && (int64_t)(uint32_t)cw >= nblk;
+                    if ((uint32_t)(pw >> 32) != epoch || done) f_sm = -1;  // nothing to join here
+                    else f_B = (int)(uint32_t)pw;
+                }
+            }
+            __syncthreads();
+            const int f = f_sm;
+            const int steps = f_B;
+            __syncthreads();
+            if (f == -2) break;  // past the end of the list
+            if (f < 0) continue;
+            const int64_t off0 = bp.offsets[f];
+            const int64_t Pf = bp.offsets[f + 1] - off0;
+            const float* lw = bp.lw + off0;
+            const bool staged = Pf <= kMetroBStage;
+            if (staged) stage_weights<kMetroBThreads>(lw, Pf, wsm, red, bp.ctl);
+            const uint64_t seed = bp.seeds[f];
+            run_claimed_blocks<ROUNDS>(bp, lw, wsm, staged, Pf, off0, steps, f, epoch, (uint32_t)(seed & 0xffffffffu),
+                               (uint32_t)(seed >> 32), &blk_sm);
+            __syncthreads();  // the staging buffer is reused by the next listed filter
+        }
     }
     if (tid == 0) {
         __threadfence();
@@ -339,17 +469,25 @@ __global__ void __launch_bounds__(kMetroBThreads) k_batched_metropolis(BatchPara
 
 int batched_metropolis_blocks_per_sm() {
     const size_t smem = kMetroBStage * sizeof(float);
-    if (cudaFuncSetAttribute(k_batched_metropolis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    int nb10 = 0, nb7 = 0;
+    if (cudaFuncSetAttribute(k_batched_metropolis<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_batched_metropolis<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
         return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched_metropolis, kMetroBThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb10, k_batched_metropolis<10>, kMetroBThreads, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb7, k_batched_metropolis<7>, kMetroBThreads, smem) !=
+            cudaSuccess)
         return 0;
-    return nb;
+    return nb10 < nb7 ? nb10 : nb7;
 }
 
 cudaError_t launch_batched_metropolis(const BatchParams& bp, int grid, cudaStream_t s) {
-    k_batched_metropolis<<<grid, kMetroBThreads, kMetroBStage * sizeof(float), s>>>(bp);
+    if (bp.rounds == 7)
+        k_batched_metropolis<7><<<grid, kMetroBThreads, kMetroBStage * sizeof(float), s>>>(bp);
+    else
+        k_batched_metropolis<10><<<grid, kMetroBThreads, kMetroBStage * sizeof(float), s>>>(bp);
     return cudaGetLastError();
 }
 

@@ -343,6 +343,19 @@ cudaError_t probe_l2_random_reads(const float* buf, int64_t n, int reads, int nu
     return cudaGetLastError();
 }
 
+// Diagnostic: the tile weights the scans use, out[i] = exp(lw[i] - k ln 2).
+__global__ void k_tile_weights(const float* __restrict__ lw, int64_t n, int k, float* __restrict__ out) {
+    const fpair R = tile_reference(k);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = weight_rel(lw[i], R);
+}
+
+cudaError_t launch_tile_weights(const float* lw, int64_t n, int k, float* out, cudaStream_t s) {
+    const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    k_tile_weights<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(lw, n, k, out);
+    return cudaGetLastError();
+}
+
 int reduce_tiles(int64_t P) { return (int)((P + kRedTile - 1) / kRedTile); }
 size_t reduce_record_bytes() { return sizeof(RedRecord); }
 

@@ -8,8 +8,14 @@
 // device memory, real-time loops where a first-call cudaMalloc (which also
 // synchronises the device) would stall a deadline, or builds that forbid
 // allocations once the application has started.  pf_resample_multinomial_static
-// runs the same kernel with its scratch in the fixed array below, which exists
-// from the moment the library is loaded on a device until the process exits.
+// runs the single-launch multinomial kernel with the plain binary search per
+// draw (not the binned draws of pf_resample_multinomial, whose bins would need
+// several times more scratch; both give the same ancestors) with its scratch in
+// the fixed array below.  The array belongs to the library's device code: CUDA
+// loads that module on a device lazily, at the first call that needs it, so the
+// first call on each device (which also looks up the array's address) is the
+// one that may allocate or synchronise inside the driver, and should be made at
+// start-up, outside any deadline and before any stream capture.
 #include <cstring>
 #include <mutex>
 
@@ -23,7 +29,7 @@ namespace {
 // Layout of the fixed scratch array: control words, tile records, cumulative weights.
 constexpr int kStaticTiles = 1024;
 constexpr size_t kCtlBytes = 256;
-constexpr size_t kSlotBytes = (size_t)kStaticTiles * 4 * sizeof(uint64_t);
+constexpr size_t kSlotBytes = (size_t)kStaticTiles * 16;  // one 16-byte record per tile
 constexpr size_t kVBytes = (size_t)PF_STATIC_MAX_PARTICLES * sizeof(float);
 constexpr size_t kScratchBytes = kCtlBytes + kSlotBytes + kVBytes;
 
@@ -104,7 +110,7 @@ extern "C" pf_status pf_resample_multinomial_static(const float* logw, int64_t P
     p.filter = 0;
     p.ctl = ctl;
     p.slots = reinterpret_cast<uint64_t*>(d->scratch + kCtlBytes);
-    p.wait_ns = 1000000000ull;
+    p.wait_ns = current_wait_ns();
     p.skip_tile = -1;
     p.v_out = reinterpret_cast<float*>(d->scratch + kCtlBytes + kSlotBytes);
     if (launch_sorted_persistent(PF_MULTINOMIAL, p, (int)g, s) != cudaSuccess) return PF_ERR_CUDA;

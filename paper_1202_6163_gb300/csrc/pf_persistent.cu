@@ -74,9 +74,9 @@ __host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T, int 
 // Arrive on this epoch's counter with release semantics (after the CTA's
 // records are written) and wait, one thread, bounded, for every CTA.
 __device__ bool arrive_and_wait(const SortedParams& p, PersistShared& sm, bool skip, uint32_t epoch,
-                                uint64_t t_start, int counters = CTL_ARRIVE0) {
+                                uint64_t t_start) {
     const int tid = threadIdx.x;
-    uint32_t* arrive = p.ctl + counters + (epoch & 1u);
+    uint32_t* arrive = p.ctl + CTL_ARRIVE0 + (epoch & 1u);
     if (tid == 0) {
         if (!skip) red_release_add_u32(arrive, 1u);
         int ok = 1;
@@ -449,346 +449,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         __syncthreads();
         trace_stamp(p.trace, p.trace_cap, blockIdx.x, 4);
     }
-}
-
-// ---------------------------------------------------------------------------
-// Multinomial by binned draws (Figure 1a; the binary search of Section 3, run
-// on draws grouped by tile).  After the tile scan and the carries, each CTA:
-//   2a. counts its slice of the P draws by target tile (shared-memory
-//       counters; the tile of a draw from the table of boundaries);
-//   2r. reserves room for them in each tile's bin with one global atomic per
-//       (CTA, tile);
-//   2b. draws them again and writes (j, Philox word) into its reserved slots;
-//       a draw that finds its bin full (bins hold the tile's expected count
-//       P S_t / W plus six standard deviations plus 32, so this is rare) is
-//       resolved at once by a binary search over the tile's cumulative weights
-//       in global memory;
-// then, after a second grid-wide wait,
-//   3.  takes an equal share of the bin positions, stages the cumulative
-//       weights of each tile it meets in shared memory, and resolves the draws
-//       there: the same lower-bound search on the same monotone sequence as
-//       the direct search, so the same ancestors.
-// ---------------------------------------------------------------------------
-// Shared memory after PersistShared: table[T] (TableEntry), boff[T+1]
-// (bin starts), cnt[T], base[T] (ints, each array padded to 4), then a
-// region used first for the tile lookup lut[kLut+1] and later for one tile's
-// cumulative weights (tile floats).
-__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
-__host__ __device__ constexpr size_t mb_region_bytes(int tile) {
-    return (size_t)((kLut + 1) * 4 > tile * 4 ? pad4(kLut + 1) * 4 : pad4(tile) * 4);
-}
-size_t multinomial_binned_smem(int T, int tile) {
-    return sizeof(PersistShared) + (size_t)T * sizeof(TableEntry) + (size_t)(pad4(T + 1) + 2 * pad4(T)) * 4 +
-           mb_region_bytes(tile);
-}
-
-int64_t multinomial_bin_cap(int64_t P, int T) {
-    // sum over tiles of lambda_t + 6 sqrt(lambda_t) + 33 <= P + 6 sqrt(P T) + 33 T, plus slack for rounding
-    return P + (int64_t)ceil(6.0 * sqrt((double)P * (double)T)) + 34LL * T + P / 256 + 1024;
-}
-
-// The tile whose cumulative interval holds the target (th, tl): the tiles between
-// the lookup points around the uniform, confirmed (else a full search; the
-// predicate is monotone in t), and never a tile without weight.
-__device__ __forceinline__ int draw_tile(uint32_t x, const TableEntry* table, const int* lut, int T, float th,
-                                         float tl) {
-    const int kq = (int)(x >> (32 - kLutBits));
-    int lo = last_tile_at_or_below(table, lut[kq], min(lut[kq + 1], T - 1), th, tl);
-    if (!boundary_at_or_below(table[lo], th, tl) || (lo + 1 < T && boundary_at_or_below(table[lo + 1], th, tl)))
-        lo = last_tile_at_or_below(table, 0, T - 1, th, tl);
-    while (lo > 0 && table[lo].il < 0) --lo;
-    return lo;
-}
-
-// Tile-local target of (th, tl) in tile entry e (clamped at the tile start).
-__device__ __forceinline__ void local_target(const TableEntry& e, float th, float tl, float& xh, float& xl) {
-    xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
-    xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
-    if (xh + xl < 0.f) {
-        xh = 0.f;
-        xl = 0.f;
-    }
-}
-
-// First element of v[0..n) whose |v| exceeds the tile-local target (xh, xl)
-// (|v| - xh is exact near the decision), moved to the next positive element
-// when rounding lands on a zero weight; il (the tile's last positive element)
-// when none exceeds it.  GLOBAL: v in global memory (L2), else shared.
-template <bool GLOBAL>
-__device__ __forceinline__ int search_tile(const float* v, int n, int il, float xh, float xl) {
-    auto ld = [&](int i) -> float { return GLOBAL ? __ldcg(v + i) : v[i]; };
-    int lo = 0, cnt = n;
-    while (cnt > 0) {
-        const int half = cnt >> 1;
-        if (__fsub_rn(fabsf(ld(lo + half)), xh) > xl) {
-            cnt = half;
-        } else {
-            lo += half + 1;
-            cnt -= half + 1;
-        }
-    }
-    if (lo >= n) return il;
-    if (zero_flag(ld(lo))) {
-        for (int z = lo + 1; z < n; ++z)
-            if (!zero_flag(ld(z))) return z;
-        return il;
-    }
-    return lo;
-}
-
-// Block-wide exclusive prefix sum of a[0..n) in place (n <= 8 * kThreads);
-// a[n] receives the total.  red: kWarps ints.
-__device__ void block_excl_scan(int* a, int n, int* red) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int per = 8;
-    int loc[per], sum = 0;
-#pragma unroll
-    for (int i = 0; i < per; ++i) {
-        const int k = tid * per + i;
-        loc[i] = k < n ? a[k] : 0;
-        sum += loc[i];
-    }
-    int inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int h = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += h;
-    }
-    if (lane == 31) red[warp] = inc;
-    __syncthreads();
-    int wb = lane < kWarps ? red[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < kWarps; o <<= 1) {
-        const int h = __shfl_up_sync(0xffffffffu, wb, o);
-        if (lane >= o) wb += h;
-    }
-    const int total = __shfl_sync(0xffffffffu, wb, kWarps - 1);
-    int run = (warp > 0 ? __shfl_sync(0xffffffffu, wb, warp - 1) : 0) + inc - sum;
-#pragma unroll
-    for (int i = 0; i < per; ++i) {
-        const int k = tid * per + i;
-        if (k < n) a[k] = run;
-        run += loc[i];
-    }
-    if (tid == 0) a[n] = total;
-    __syncthreads();
-}
-
-template <int KK>
-__global__ void __launch_bounds__(kThreads, 2) k_multinomial_binned(SortedParams p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
-    const int T = p.n_tiles;
-    TableEntry* table = reinterpret_cast<TableEntry*>(smem_raw + sizeof(PersistShared));
-    int* boff = reinterpret_cast<int*>(table + T);
-    int* cnt = boff + pad4(T + 1);
-    int* base = cnt + pad4(T);
-    int* lut = base + pad4(T);
-    float* vt = reinterpret_cast<float*>(lut);  // phase 3: one tile's cumulative weights
-    const int tid = threadIdx.x, cta = blockIdx.x, G = gridDim.x;
-    const uint64_t t_start = global_ns();
-    const uint32_t epoch = ld_relaxed_u32(p.ctl + CTL_EPOCH) + 1u;
-    const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
-    const int t_first = cta * R;
-    const int t_count = max(0, min(R, T - t_first));
-    uint32_t* rec = reinterpret_cast<uint32_t*>(p.slots);
-    if (p.trace) {
-        trace_put(p.trace, p.trace_cap, cta, 0, t_start);
-        for (int w = 1; w <= 4; ++w) trace_put(p.trace, p.trace_cap, cta, w, 0);
-        trace_put(p.trace, p.trace_cap, cta, 5, cta);
-        trace_put(p.trace, p.trace_cap, cta, 6, 0);
-        trace_put(p.trace, p.trace_cap, cta, 7, (uint64_t)t_count);
-    }
-    // 1. scan every owned tile: cumulative weights to global memory, one record per tile
-    TileThread th;
-    const int64_t PA = p.P + p.lead;
-    if (tid < t_count) p.cursors[t_first + tid] = 0u;  // this launch's bins start empty
-    for (int r = 0; r < t_count; ++r) {
-        const int t = t_first + r;
-        const int64_t t0 = (int64_t)t * p.tile;
-        const int n = (int)min((int64_t)p.tile, PA - t0);
-        const TileSummary ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
-        if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
-        write_tile_v<KK>(p, th, t0, n);
-        __threadfence();
-        if (tid == 0)
-            st_v4_u32(rec + 4 * t, (uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo),
-                      (uint32_t)ts.i_last);
-        __syncthreads();
-    }
-    trace_stamp(p.trace, p.trace_cap, cta, 1);
-    bool ok = arrive_and_wait(p, sm, false, epoch, t_start);
-    trace_stamp(p.trace, p.trace_cap, cta, 2);
-    if (!ok && tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
-    if (ok) ok = carries<KIND_MULTI>(p, sm, table, t_first, t_count);
-    if (cta == 0 && tid == 0) {
-        atomicExch(p.ctl + CTL_ARRIVE0 + ((epoch + 1u) & 1u), 0u);
-        atomicExch(p.ctl + CTL_EPOCH, epoch);
-    }
-    if (!ok) return;
-    const float Wh = sm.as.W_hi, Wl = sm.as.W_lo;
-    build_tile_lut(table, T, Wh, Wl, lut, sm.red_k);
-    // bin capacities: the tile's expected count P S_t / W plus 6 sigma plus 32
-    // (every CTA forms the same integers from the same bits), then bin starts
-    for (int t = tid; t < T; t += kThreads) {
-        int cap = 0;
-        if (table[t].il >= 0) {
-            const float nh = t + 1 < T ? table[t + 1].bhi : Wh, nl = t + 1 < T ? table[t + 1].blo : Wl;
-            const float frac = __fdiv_rn(__fadd_rn(__fsub_rn(nh, table[t].bhi), __fsub_rn(nl, table[t].blo)), Wh);
-            const float lam = fmaxf(frac, 0.f) * (float)p.P;
-            cap = (int)fminf(ceilf(lam + 6.f * sqrtf(lam) + 32.f), 2147483647.f / 8.f);
-        }
-        boff[t] = cap;
-        cnt[t] = 0;
-    }
-    __syncthreads();
-    block_excl_scan(boff, T, sm.red_k);
-    const bool binned = (int64_t)boff[T] <= p.bin_cap;  // always, by the bound the host sized the bins with
-    trace_stamp(p.trace, p.trace_cap, cta, 3);
-
-    const int64_t nq = (p.P + 3) >> 2;  // four draws per Philox block
-    const int64_t q_beg = nq * cta / G, q_end = nq * (cta + 1) / G;
-    const float* vg = p.v_out;
-    // 2a. count this CTA's draws by tile
-    if (binned) {
-        for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
-            const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                if (4 * q + s >= p.P) break;
-                const uint32_t x = word_of(r, s);
-                float uh, ul, th2, tl2;
-                u32_pair(x, uh, ul);
-                draw_target(uh, ul, Wh, Wl, th2, tl2);
-                atomicAdd(&cnt[draw_tile(x, table, lut, T, th2, tl2)], 1);
-            }
-        }
-        __syncthreads();
-        // 2r. one reservation per tile this CTA draws into
-        for (int t = tid; t < T; t += kThreads)
-            if (cnt[t] > 0) base[t] = (int)atomicAdd(p.cursors + t, (uint32_t)cnt[t]);
-        __syncthreads();
-    }
-    // 2b. the draws again, into their slots (or resolved at once when the bin is full)
-    for (int64_t q = q_beg + tid; q < q_end; q += kThreads) {
-        const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int64_t j = 4 * q + s;
-            if (j >= p.P) break;
-            const uint32_t x = word_of(r, s);
-            float uh, ul, th2, tl2;
-            u32_pair(x, uh, ul);
-            draw_target(uh, ul, Wh, Wl, th2, tl2);
-            const int t = draw_tile(x, table, lut, T, th2, tl2);
-            if (binned) {
-                const int slot = base[t] + atomicSub(&cnt[t], 1) - 1;
-                if (slot < boff[t + 1] - boff[t]) {
-                    p.bins[boff[t] + slot] = make_int2((int)j, (int)x);
-                    continue;
-                }
-            }
-            float xh, xl;
-            local_target(table[t], th2, tl2, xh, xl);
-            const int64_t b0 = (int64_t)t * p.tile;
-            const int idx = search_tile<true>(vg + b0, (int)min((int64_t)p.tile, PA - b0), table[t].il, xh, xl);
-            p.anc[j] = (int32_t)(b0 + idx - p.lead);
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    ok = arrive_and_wait(p, sm, false, epoch, t_start, CTL_ARRIVE2_0);
-    if (cta == 0 && tid == 0) atomicExch(p.ctl + CTL_ARRIVE2_0 + ((epoch + 1u) & 1u), 0u);
-    if (!ok) {
-        if (tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
-        return;
-    }
-    // 3. an equal share of the bin positions; each tile met is staged once
-    if (binned) {
-        const int64_t C = boff[T];
-        const int64_t p0 = C * cta / G, p1 = C * (cta + 1) / G;
-        int lo = 0, hi = T - 1;  // last tile whose bin starts at or before p0
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (boff[mid] <= p0) lo = mid;
-            else hi = mid - 1;
-        }
-        __syncthreads();  // lut (aliased by vt) is no longer read
-        for (int t = lo; t < T && (int64_t)boff[t] < p1; ++t) {
-            const int64_t s0 = max(p0, (int64_t)boff[t]);
-            const int64_t filled = min((int64_t)__ldcg(p.cursors + t), (int64_t)(boff[t + 1] - boff[t]));
-            const int64_t s1 = min(p1, (int64_t)boff[t] + filled);
-            if (s1 <= s0) continue;  // uniform over the block
-            const int64_t b0 = (int64_t)t * p.tile;
-            const int n = (int)min((int64_t)p.tile, PA - b0);
-            for (int i = 4 * tid; i < n; i += 4 * kThreads) {
-                if (i + 3 < n) {
-                    *reinterpret_cast<float4*>(vt + i) = __ldcg(reinterpret_cast<const float4*>(vg + b0 + i));
-                } else {
-                    for (int z = i; z < n; ++z) vt[z] = __ldcg(vg + b0 + z);
-                }
-            }
-            __syncthreads();
-            const TableEntry e = table[t];
-            for (int64_t k = s0 + tid; k < s1; k += kThreads) {
-                const int2 d = __ldcg(p.bins + k);
-                float uh, ul, th2, tl2, xh, xl;
-                u32_pair((uint32_t)d.y, uh, ul);
-                draw_target(uh, ul, Wh, Wl, th2, tl2);
-                local_target(e, th2, tl2, xh, xl);
-                p.anc[d.x] = (int32_t)(b0 + search_tile<false>(vt, n, e.il, xh, xl) - p.lead);
-            }
-            __syncthreads();  // vt is reloaded for the next tile
-        }
-    }
-    if (p.trace) {
-        __syncthreads();
-        trace_stamp(p.trace, p.trace_cap, cta, 4);
-    }
-}
-
-template <int KK>
-static cudaError_t launch_mb(const SortedParams& p, int grid, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = multinomial_binned_smem(p.n_tiles, p.tile);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_multinomial_binned<KK>, p);
-}
-
-cudaError_t launch_multinomial_binned(const SortedParams& p, int grid, cudaStream_t s) {
-    const int R = p.tiles_per_cta > 0 ? p.tiles_per_cta : 1;
-    if (p.n_tiles < 1 || p.n_tiles > kMaxTilesTotal || R > kMaxOwn || (int64_t)grid * R < p.n_tiles ||
-        p.tile < 4 || p.tile > kTileMax || grid > kThreads || !p.bins || !p.cursors || !p.v_out)
-        return cudaErrorInvalidValue;
-    const int q = (p.tile + kThreads - 1) / kThreads;
-    if (q <= 4) return launch_mb<4>(p, grid, s);
-    if (q <= 8) return launch_mb<8>(p, grid, s);
-    return launch_mb<16>(p, grid, s);
-}
-
-// Resident CTAs per SM of the binned kernel at `smem` bytes (the smallest
-// over the three widths); raises their shared-memory limits on the way.
-int multinomial_binned_blocks_per_sm(size_t smem) {
-    int best = 1 << 30;
-    cudaError_t e = cudaSuccess;
-    auto one = [&](auto kern) {
-        int nb = 0;
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)multinomial_binned_smem(kMaxTilesTotal, kTileMax));
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem);
-        best = min(best, nb);
-    };
-    one(k_multinomial_binned<4>);
-    one(k_multinomial_binned<8>);
-    one(k_multinomial_binned<16>);
-    return e == cudaSuccess ? best : 0;
 }
 
 template <int KIND, int KK>

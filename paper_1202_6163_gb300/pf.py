@@ -50,6 +50,9 @@ SIGNATURES = {
     "pf_get_min_tile": (_INT, [_INT, _I64]),
     "pf_resample_batched_masked": (_INT, [_INT, _VP, _VP, _INT, _INT, _VP, _VP, _VP, _VP]),
     "pf_resample_batched_metropolis_bound": (_INT, [_VP, _VP, _INT, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
+    "pf_set_metropolis_philox_rounds": (_INT, [_INT]),
+    "pf_debug_tile_weights": (_INT, [_VP, _I64, _INT, _VP, _VP]),
+    "pf_get_metropolis_philox_rounds": (_INT, []),
     "pf_lg_init": (_INT, [_INT, _I64, _INT, ctypes.c_float, ctypes.c_float, _U64, _VP, _VP, _VP, _VP, _VP, _VP,
                           _VP]),
     "pf_lg_step": (_INT, [_INT, _I64, _INT, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _INT, _U64,
@@ -142,6 +145,19 @@ def pf_resample_batched_metropolis_bound(logw, offsets, F, eps, seeds, ancestors
     _check(load().pf_resample_batched_metropolis_bound(_ptr(logw), _ptr(offsets), F, float(eps), _ptr(seeds),
                                                        _ptr(mask), _ptr(ancestors), _ptr(B_out), _stream(stream)),
            "pf_resample_batched_metropolis_bound")
+
+
+def pf_debug_tile_weights(logw, n, k, weights, stream=None):
+    _check(load().pf_debug_tile_weights(_ptr(logw), n, int(k), _ptr(weights), _stream(stream)),
+           "pf_debug_tile_weights")
+
+
+def pf_set_metropolis_philox_rounds(rounds):
+    _check(load().pf_set_metropolis_philox_rounds(int(rounds)), "pf_set_metropolis_philox_rounds")
+
+
+def pf_get_metropolis_philox_rounds():
+    return int(load().pf_get_metropolis_philox_rounds())
 
 
 def pf_resample_batched_masked(kind, logw, offsets, F, B, seeds, mask, ancestors, stream=None):

@@ -169,9 +169,10 @@ def _replay(lw64, P, k, props, unifs, b0, flips_left, target, tau):
 
 
 def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TAU, max_flips=3,
-                     draws=None) -> ParityReport:
+                     draws=None, rounds=10) -> ParityReport:
     """a_gpu, a_orc: ancestors of the chains listed in `chains` (all chains if None).
-    draws: (proposals, uniforms), each of shape (P, B), in place of the library's streams."""
+    draws: (proposals, uniforms), each of shape (P, B), in place of the library's streams;
+    rounds: the Philox rounds of those streams (10, or 7 for the opt-in stream)."""
     lw = np.asarray(lw, dtype=np.float32)
     lw64 = lw.astype(np.float64)
     P = lw.size
@@ -187,7 +188,7 @@ def check_metropolis(lw, B, a_gpu, a_orc, seed, chains=None, filter_id=0, tau=TA
     for q in mism:
         i = int(idx[q])
         if draws is None:
-            props, unifs = oracle.metropolis_draws(seed, filter_id, P, i, B)
+            props, unifs = oracle.metropolis_draws(seed, filter_id, P, i, B, rounds=rounds)
         else:
             props, unifs = draws[0][i], draws[1][i]
         flips = _replay(lw64, P, i, props, unifs, 0, max_flips, int(a_gpu[q]), tau)

@@ -78,6 +78,10 @@ CHILD = textwrap.dedent(r"""
     add("pf_reserve", 0, 0, -1, None)
     add("pf_get_device_status", None, None)           # null out
     add("pf_set_wait_limit_ns", 0)
+    add("pf_debug_tile_weights", A, 0, 0, B_, None)
+    add("pf_debug_tile_weights", A, 16, (1 << 24) + 1, B_, None)
+    add("pf_set_metropolis_philox_rounds", 8)
+    add("pf_set_metropolis_philox_rounds", 0)
     add("pf_set_trace_buffer", A + 4, 64)             # not 8-byte aligned
     add("pf_set_trace_buffer", A, 0)                  # buffer without capacity
     add("pf_set_trace_buffer", None, -1)

@@ -125,3 +125,48 @@ def test_index_draws_uniform():
     counts = np.bincount(prop, minlength=P)
     assert counts.size == P
     assert stats.chisquare(counts).pvalue > 1e-4
+
+
+# ------------------------------------------------- Philox-4x32-7 (the opt-in Metropolis stream)
+def test_round_generic_philox_is_the_pinned_generator_at_ten_rounds():
+    # the round-generic function at 10 rounds is the generator pinned to cuRAND
+    # above, so the seven-round stream is the same round function stopped earlier
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        c = [int(x) for x in rng.integers(0, 1 << 32, 4, dtype=np.uint64)]
+        k = [int(x) for x in rng.integers(0, 1 << 32, 2, dtype=np.uint64)]
+        assert list(oracle.philox4x32(c, k, 10)) == list(oracle.philox4x32_10(c, k))
+        assert list(oracle.philox4x32(c, k, 7)) != list(oracle.philox4x32_10(c, k))
+        assert list(oracle.philox4x32(c, k, 0)) == c  # no round: the counter itself
+
+
+def test_seven_rounds_every_word_matters_and_output_is_uniform():
+    base_c, base_k = [5, 6, 7, 8], [9, 10]
+    ref = oracle.philox4x32(base_c, base_k, 7)
+    for w in range(4):
+        c = list(base_c)
+        c[w] ^= 1
+        assert all(a != b for a, b in zip(oracle.philox4x32(c, base_k, 7), ref)), w
+    for w in range(2):
+        k = list(base_k)
+        k[w] ^= 1
+        assert all(a != b for a, b in zip(oracle.philox4x32(base_c, k, 7), ref)), w
+    # consecutive counters: every output word uniform, and its bits balanced
+    words = np.array([oracle.philox4x32([q, 0, 3, oracle.TAG_METRO], [77, 0], 7) for q in range(8192)],
+                     dtype=np.uint64)
+    for s in range(4):
+        counts = np.bincount((words[:, s] >> np.uint64(26)).astype(np.int64), minlength=64)
+        assert stats.chisquare(counts).pvalue > 1e-4, s
+        bits = ((words[:, s][:, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1)).mean(0)
+        assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / np.sqrt(words.shape[0])), s
+
+
+def test_seven_round_metropolis_draw_layout():
+    seed, f, P, i, B = 99, 3, 1000, 17, 5
+    prop, unif = oracle.metropolis_draws(seed, f, P, i, B, rounds=7)
+    key = [seed, 0]
+    for b in range(B):
+        r = oracle.philox4x32([i, b // 2, f, oracle.TAG_METRO], key, 7)
+        x_j, x_u = (r[0], r[1]) if b % 2 == 0 else (r[2], r[3])
+        assert prop[b] == (int(x_j) * P) >> 32
+        assert unif[b] == oracle.u23(int(x_u))

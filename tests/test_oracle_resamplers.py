@@ -397,3 +397,32 @@ def test_orc_batched_is_the_per_filter_calls_with_their_filter_ids():
                 assert np.all(o >= np.floor(e - 1e-9)) and np.all(o <= np.ceil(e + 1e-9)), f
         if kind in (0, 3):
             assert not np.array_equal(a[off[4]:off[5]], a[off[5]:off[6]])
+
+
+# ----------------------------------------------- Metropolis on the seven-round stream
+def test_seven_round_metropolis_identity_and_last_proposal():
+    lw = workloads.gaussian_logw(100, seed=1)
+    assert np.array_equal(oracle.metropolis(lw, 0, 5, rounds=7), np.arange(100))
+    P, B = 50, 7
+    a = oracle.metropolis(np.zeros(P, np.float32), B, 9, rounds=7)
+    for i in range(P):
+        prop, _ = oracle.metropolis_draws(9, 0, P, i, B, rounds=7)
+        assert a[i] == prop[-1]
+    assert not np.array_equal(a, oracle.metropolis(np.zeros(P, np.float32), B, 9))  # another stream
+
+
+@pytest.mark.parametrize("B", [1, 3])
+def test_seven_round_metropolis_law_matches_matrix_power(B):
+    lw = _lw(0.0, 1.0, -1.0, 0.5)
+    P = lw.size
+    MB = np.linalg.matrix_power(oracle.metropolis_matrix(lw), B)
+    n = 20000
+    counts = np.zeros((P, P))
+    for seed in range(n):
+        a = oracle.metropolis(lw, B, seed, rounds=7)
+        counts[np.arange(P), a] += 1
+    for i in range(P):
+        exp = n * MB[i]
+        keep = exp > 0
+        assert counts[i][~keep].sum() == 0
+        assert stats.chisquare(counts[i][keep], exp[keep]).pvalue > 1e-4
