@@ -428,7 +428,9 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     const int grid = info->num_sms * per_sm;
     // scratch: per-CTA cumulative weights (multinomial), the plan's items, the
     // split filters' tile records; two counters per filter
-    const int64_t per_cta = kind == PF_MULTINOMIAL ? (int64_t)batched_scratch_floats_per_cta() : 0;
+    // per-CTA scratch: the cumulative weights of a whole filter's tiles (multinomial, and
+    // systematic / stratified filters kept whole in one CTA)
+    const int64_t per_cta = kind != PF_METROPOLIS ? (int64_t)batched_scratch_floats_per_cta() : 0;
     const size_t items_at = ((size_t)grid * per_cta * sizeof(float) + 255) & ~(size_t)255;
     const size_t n_items = (size_t)F * kMaxItemsPerFilter;
     const size_t records_at = (items_at + n_items * sizeof(int32_t) + 255) & ~(size_t)255;
@@ -443,7 +445,7 @@ pf_status resample_batched(int kind, const float* logw, const int64_t* offsets, 
     }
     int32_t* items = reinterpret_cast<int32_t*>((char*)w->scratch + items_at);
     const int split = kind == PF_STRATIFIED || kind == PF_SYSTEMATIC;
-    cudaError_t e = launch_batched_plan(logw, offsets, F, mask, split, items, w->ctl, s, kind == PF_METROPOLIS);
+    cudaError_t e = launch_batched_plan(logw, offsets, F, mask, split, items, w->ctl, s, kind == PF_METROPOLIS, grid);
     if (e != cudaSuccess) return cuda_fail(e, "batched plan launch");
     BatchParams bp;
     bp.lw = logw;
@@ -505,7 +507,7 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     if (red > need) need = red;
     if (F_max > 0) {
         for (int k = PF_MULTINOMIAL; k <= PF_METROPOLIS; ++k) {
-            const size_t per_cta = k == PF_MULTINOMIAL ? batched_scratch_floats_per_cta() : 0;
+            const size_t per_cta = k != PF_METROPOLIS ? batched_scratch_floats_per_cta() : 0;
             const size_t items_at =
                 ((size_t)info->num_sms * info->batched_per_sm[k] * per_cta * sizeof(float) + 255) & ~(size_t)255;
             const size_t n_items = (size_t)F_max * kMaxItemsPerFilter;

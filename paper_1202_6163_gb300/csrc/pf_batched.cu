@@ -44,6 +44,7 @@ struct BatchShared {
     float rsh[kMaxOwnB], rsl[kMaxOwnB];
     int ril[kMaxOwnB];
     TableEntry table[kMaxOwnB];
+    TileMap maps[kMaxOwnB];  // systematic / stratified whole filters: each tile's offset map
     int f, skip;
 };
 // Dynamic shared memory: BatchShared, then the region -- the two run-length
@@ -153,6 +154,65 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(BatchParams bp) {
             trace_put(bp.trace, bp.trace_cap, ticket, 7, (uint64_t)c_item);
         }
 
+        if (KIND != KIND_MULTI && c_item == kWhole && Tf > 1) {
+            // ---- systematic / stratified: a whole filter of several tiles in this CTA (the plan
+            // gives whole filters when there are enough of them to occupy the grid): every tile is
+            // scanned (the cumulative weights of all but the last kept in this CTA's scratch), warp 0
+            // forms the carries, two lanes per tile the offset maps, then the tiles are assigned,
+            // last first -- no wait on any other CTA ----
+            p.v_out = bp.scratch + (int64_t)blockIdx.x * bp.scratch_per_cta;
+            TileSummary ts;
+            int bad = 0;
+            for (int c = 0; c < Tf; ++c) {
+                const int64_t t0 = (int64_t)c * kTileMax;
+                const int n = (int)min((int64_t)kTileMax, PA - t0);
+                ts = tile_scan(p.lw + t0, c == 0 ? lead : 0, n, sm.tile, th);
+                bad |= ts.bad;
+                if (tid == 0) {
+                    sm.rk[c] = ts.k;
+                    sm.rsh[c] = ts.S.hi;
+                    sm.rsl[c] = ts.S.lo;
+                    sm.ril[c] = ts.i_last;
+                }
+                if (c + 1 < Tf) write_tile_v(p, th, t0, n);  // reloaded for its assignment
+                __syncthreads();
+            }
+            trace_stamp(bp.trace, bp.trace_cap, ticket, 1);
+            trace_stamp(bp.trace, bp.trace_cap, ticket, 2);
+            if (tid < 32) {
+                const bool in = lane < Tf;
+                filter_carries<KIND>(sm, bp, Tf, lane, in ? sm.rk[lane] : 0, in ? sm.rsh[lane] : 0.f,
+                                     in ? sm.rsl[lane] : 0.f, in ? sm.ril[lane] : -1, bad, true);
+            }
+            __syncthreads();
+            if (!sm.skip) {
+                trace_stamp(bp.trace, bp.trace_cap, ticket, 3);
+                if (tid < 32) {  // Tf <= 16 pairs of lanes of warp 0
+                    const int r = min(tid >> 1, Tf - 1);
+                    const TileMap m = tile_map_pair<KIND>(p, sm.as, sm.Bown[r], sm.Bown[r + 1], sm.rk[r], 0xffffffffu);
+                    if ((tid & 1) == 0 && (tid >> 1) < Tf) sm.maps[tid >> 1] = m;
+                }
+                __syncthreads();
+                for (int c = Tf - 1; c >= 0; --c) {
+                    const int64_t t0 = (int64_t)c * kTileMax;
+                    if (c != Tf - 1) read_tile_v(p.v_out + t0, (int)min((int64_t)kTileMax, PA - t0), th);
+                    ts.i_last = sm.ril[c];
+                    const TileMap map = sm.maps[c];
+                    if (th.K == 16)
+                        assign_offspring<KIND, 16>(p, sm.as, map, stage, chunks, th, ts, t0 - lead);
+                    else if (th.K == 8)
+                        assign_offspring<KIND, 8>(p, sm.as, map, stage, chunks, th, ts, t0 - lead);
+                    else
+                        assign_offspring<KIND, 4>(p, sm.as, map, stage, chunks, th, ts, t0 - lead);
+                }
+                if (bp.trace) {
+                    __syncthreads();
+                    trace_stamp(bp.trace, bp.trace_cap, ticket, 4);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         if (KIND != KIND_MULTI) {
             // ---- systematic / stratified: one tile (a one-tile filter is its own item) ----
             const int c = c_item == kWhole ? 0 : c_item;
@@ -339,8 +399,9 @@ constexpr int kPlanThreads = 1024;
 __global__ void __launch_bounds__(kPlanThreads) k_batched_plan(const float* __restrict__ lw,
                                                                const int64_t* __restrict__ offsets, int F,
                                                                const int32_t* __restrict__ mask, int split,
-                                                               int32_t* __restrict__ items, uint32_t* ctl, int metro) {
-    __shared__ int count[kMaxOwnB + 1], start[kMaxOwnB + 1];
+                                                               int32_t* __restrict__ items, uint32_t* ctl, int metro,
+                                                               int split_min) {
+    __shared__ int count[kMaxOwnB + 1], start[kMaxOwnB + 1], split_sm;
     const int tid = threadIdx.x;
     if (tid <= kMaxOwnB) count[tid] = 0;
     if (metro) {
@@ -373,18 +434,24 @@ __global__ void __launch_bounds__(kPlanThreads) k_batched_plan(const float* __re
     }
     __syncthreads();
     if (tid == 0) {
+        // several-tile filters are split over CTAs only while they are too few to occupy the grid
+        int multi = 0;
+        for (int T = 2; T <= kMaxOwnB; ++T) multi += count[T];
+        const int sp = split && multi < split_min;
+        split_sm = sp;
         int run = 0;
         for (int T = kMaxOwnB; T >= 1; --T) {
             start[T] = run;
-            run += count[T] * (split && T > 1 ? T : 1);
+            run += count[T] * (sp && T > 1 ? T : 1);
         }
         ctl[CTL_ITEMS] = (uint32_t)run;
     }
     __syncthreads();
+    const int sp = split_sm;
     for (int f = tid; f < F; f += kPlanThreads) {
         const int T = tiles(f);
         if (!T) continue;
-        const int per = split && T > 1 ? T : 1;
+        const int per = sp && T > 1 ? T : 1;
         const int at = atomicAdd(&start[T], per);
         if (per == 1) {
             items[at] = f * 32 + kWhole;
@@ -395,8 +462,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_batched_plan(const float* __re
 }
 
 cudaError_t launch_batched_plan(const float* lw, const int64_t* offsets, int F, const int32_t* mask, int split,
-                                int32_t* items, uint32_t* ctl, cudaStream_t s, int metro) {
-    k_batched_plan<<<1, kPlanThreads, 0, s>>>(lw, offsets, F, mask, split, items, ctl, metro);
+                                int32_t* items, uint32_t* ctl, cudaStream_t s, int metro, int split_min) {
+    k_batched_plan<<<1, kPlanThreads, 0, s>>>(lw, offsets, F, mask, split, items, ctl, metro, split_min);
     return cudaGetLastError();
 }
 

@@ -159,7 +159,7 @@ cudaError_t launch_gather_inplace(void* x, int64_t P, int64_t row_bytes, const i
 int persistent_blocks_per_sm(int kind);
 cudaError_t launch_batched(int kind, const BatchParams& bp, int grid, cudaStream_t s);
 cudaError_t launch_batched_plan(const float* lw, const int64_t* offsets, int F, const int32_t* mask, int split,
-                                int32_t* items, uint32_t* ctl, cudaStream_t s, int metro = 0);
+                                int32_t* items, uint32_t* ctl, cudaStream_t s, int metro = 0, int split_min = 0);
 constexpr int kMaxHeavy = 4096;  // batched Metropolis: length of the list of shared filters
 constexpr int kMaxItemsPerFilter = 16;  // tiles of a batched filter (kMaxOwnB)
 int batched_blocks_per_sm(int kind);

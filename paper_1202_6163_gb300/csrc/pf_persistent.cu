@@ -52,6 +52,7 @@ struct PersistShared {
     int own_k[kMaxOwn], own_il[kMaxOwn];
     int red_k[kWarps];
     int ok;
+    uint64_t bar[2];  // completion of the tile copies into the two staging buffers (pass 1)
 };
 // Dynamic shared memory: PersistShared, then either the two staging buffers
 // int32 stage[2 * kIoCap] (systematic, stratified) or, for multinomial, TableEntry
@@ -358,20 +359,58 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     }
 
     static_assert(sizeof(PersistShared) % 16 == 0, "the staging buffers are 16-byte aligned");
-    if (KIND != KIND_MULTI) stage_init<stage_cap(KK)>(reinterpret_cast<int32_t*>(region));  // before pass 2's barriers
+    // the staging buffers start pass 2 at -1 (below every decode tag); with tile
+    // copies in pass 1 they are set after it
+    if (KIND != KIND_MULTI && t_count <= 1) stage_init<stage_cap(KK)>(reinterpret_cast<int32_t*>(region));
 
-    // pass 1: scan and record every owned tile
+    // pass 1: scan and record every owned tile.  Systematic / stratified with
+    // several tiles per CTA: tile r + 1 is bulk-copied into one of the two
+    // staging buffers (idle until pass 2) while tile r is scanned from the other.
     TileThread th;
     TileSummary ts;
     ts.k = 0;
     ts.i_last = -1;
     bool skip = false;
     const int64_t PA = p.P + p.lead;  // length of the aligned window
+    constexpr bool kCopies = KIND != KIND_MULTI;
+    const bool copies = kCopies && t_count > 1;  // uniform over the CTA
+    float* slot = reinterpret_cast<float*>(region);
+    constexpr int kSlotFloats = stage_cap(KK);  // floats per staging buffer (>= the tile)
+    auto issue = [&](int r) {  // thread 0: the copy of owned tile r (its whole 16-byte pieces)
+        const int64_t t0 = (int64_t)(t_first + r) * p.tile;
+        const uint32_t bytes = (uint32_t)((int)min((int64_t)p.tile, PA - t0) & ~3) * 4u;
+        if (bytes) bulk_load(slot + (r & 1) * kSlotFloats, p.lw + t0, bytes, &sm.bar[r & 1]);
+        else mbar_arrive(&sm.bar[r & 1]);
+    };
+    bool copy_ok = true;
+    if (kCopies && copies) {
+        if (tid == 0) {
+            mbar_init(&sm.bar[0], 1);
+            mbar_init(&sm.bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) issue(0);
+    }
     for (int r = 0; r < t_count; ++r) {
         const int t = t_first + r;
         const int64_t t0 = (int64_t)t * p.tile;
         const int n = (int)min((int64_t)p.tile, PA - t0);
-        ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
+        if (kCopies && copies) {
+            if (tid == 0 && r + 1 < t_count) issue(r + 1);
+            if (!mbar_wait(&sm.bar[r & 1], (uint32_t)(r >> 1) & 1u, t_start, p.wait_ns)) {
+                copy_ok = false;  // a copy that never completed: reported, and this CTA stops after the wait
+                if (tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
+            }
+            const float* sl = slot + (r & 1) * kSlotFloats;
+            if ((n & 3) == 0) {
+                ts = tile_scan_k<KK, true>(sl, t == 0 ? p.lead : 0, n, sm.tile, th);
+            } else {  // a ragged last tile: its tail is not in the copy; read it from global memory
+                ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
+            }
+        } else {
+            ts = tile_scan_k<KK>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
+        }
         if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
         skip |= (t == p.skip_tile);
         if (KIND == KIND_MULTI) {
@@ -390,9 +429,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
                 sm.own_shi[r] = ts.bad ? NAN : ts.S.hi;
                 sm.own_slo[r] = ts.S.lo;
             }
+            if (kCopies && copies) fence_proxy_async_smem();  // this tile's reads before the buffer's next copy
         }
         __syncthreads();
     }
+    copy_ok = __syncthreads_and(copy_ok);
+    if (kCopies && copies && copy_ok) stage_init<stage_cap(KK)>(reinterpret_cast<int32_t*>(region));  // pass 2's tags
     int kc = 0;
     if (KIND != KIND_MULTI && warp == 0) kc = publish_cta_record(p, sm, t_count);
 
@@ -415,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
         atomicExch(p.ctl + CTL_ARRIVE0 + ((epoch + 1u) & 1u), 0u);
         atomicExch(p.ctl + CTL_EPOCH, epoch);
     }
-    if (!ok) return;
+    if (!ok || !copy_ok) return;
 
     if (KIND == KIND_MULTI) {
         multinomial_draws(p, sm, reinterpret_cast<const TableEntry*>(region));

@@ -49,22 +49,25 @@ __device__ __forceinline__ int per_thread_count(int n) {
 __device__ __forceinline__ bool zero_flag(float v) { return __float_as_uint(v) >> 31; }
 
 // Loads this thread's KK elements (tile-local e0 .. e0+KK) of base[lo..n);
-// base is 16-byte aligned.  Slots outside [lo, n) read as -inf (zero weight).
-template <int KK>
+// base is 16-byte aligned, in global memory or (SMEM) in shared memory.
+// Slots outside [lo, n) read as -inf (zero weight).
+template <int KK, bool SMEM = false>
 __device__ __forceinline__ void tile_load_k(const float* __restrict__ base, int lo, int n, int e0,
                                             float (&x)[kMaxPerThread]) {
 #pragma unroll
     for (int q = 0; q < KK / 4; ++q) {
         const int idx = e0 + 4 * q;
         if (idx >= lo && idx + 3 < n) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(base + idx));
+            const float4 v = SMEM ? *reinterpret_cast<const float4*>(base + idx)
+                                  : __ldg(reinterpret_cast<const float4*>(base + idx));
             x[4 * q + 0] = v.x;
             x[4 * q + 1] = v.y;
             x[4 * q + 2] = v.z;
             x[4 * q + 3] = v.w;
         } else {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) x[4 * q + r] = (idx + r >= lo && idx + r < n) ? __ldg(base + idx + r) : -INFINITY;
+            for (int r = 0; r < 4; ++r)
+                x[4 * q + r] = (idx + r >= lo && idx + r < n) ? (SMEM ? base[idx + r] : __ldg(base + idx + r)) : -INFINITY;
         }
     }
 }
@@ -73,7 +76,7 @@ __device__ __forceinline__ void tile_load_k(const float* __restrict__ base, int 
 // first `lo` slots taken as zero weights; fills th (this thread's elements) and
 // returns the tile summary (identical in every thread).
 // KK elements per thread (n <= KK * kThreads); tile_scan picks KK from n.
-template <int KK>
+template <int KK, bool SMEM = false>  // SMEM: base is a copy of the tile in shared memory
 __device__ __forceinline__ TileSummary tile_scan_k(const float* __restrict__ base, int lo, int n, TileShared& sm,
                                                    TileThread& th) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -84,7 +87,7 @@ __device__ __forceinline__ TileSummary tile_scan_k(const float* __restrict__ bas
     if (tid == 0) sm.i_last = -1;
 
     float* x = th.v;
-    tile_load_k<KK>(base, lo, n, e0, th.v);
+    tile_load_k<KK, SMEM>(base, lo, n, e0, th.v);
 
     // 1. tile maximum and domain check: the thread's maximum propagates NaN, so
     // one test of it finds a NaN or +inf element

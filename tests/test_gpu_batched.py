@@ -200,3 +200,23 @@ def test_batched_metropolis_takes_each_filters_own_bound():
             pf.pf_resample_batched(pf.PF_METROPOLIS, d_lw, d_off, F, -1, d_seeds, anc2)
             assert pf.pf_get_device_status() == pf.PF_OK
             assert torch.equal(anc, anc2)
+
+
+@pytest.mark.parametrize("name", ["systematic", "stratified"])
+def test_batched_whole_filters_when_they_fill_the_grid(name):
+    # with at least as many several-tile filters as resident CTAs (304 on GB300) the plan keeps
+    # each filter whole in one CTA (no wait on other CTAs); ragged sizes around tile boundaries,
+    # unaligned offsets, one-tile filters between them, every filter against the oracle
+    kind, orc = KINDS[name]
+    cycle = [8193, 9001, 16384 + 7, 20000, 8189 + 8, 65536, 131069 - 8, 12345, 300, 8192]
+    sizes = [cycle[i % len(cycle)] for i in range(480)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    sf = np.resize(np.array([0.5, 1.0, 2.0, 3.0]), len(sizes))
+    lw = workloads.batched_logw(off, sf, seed=12)
+    seeds = workloads.batched_seeds(len(sizes), base=70)
+    a, st = run_batched(kind, lw, off, seeds)
+    assert st == pf.PF_OK
+    for f in range(len(sizes)):
+        l = lw[off[f]:off[f + 1]]
+        rep = check_cumulative(name, l, a[off[f]:off[f + 1]], orc(l, int(seeds[f]), f), int(seeds[f]), filter_id=f)
+        assert rep.ok, (f, sizes[f], rep.summary())
