@@ -262,6 +262,33 @@ def test_ess(P, s):
     assert ls.item() == pytest.approx(log_sum, rel=1e-12, abs=2e-6)
 
 
+@pytest.mark.parametrize("case", ["gauss_2_6M", "heavy_2e24", "dead_tiles_2e23"])
+def test_ess_large_and_dead_tiles(case):
+    # thousands of tile records in the final combine; dead_tiles has whole
+    # runs of tiles with no mass (lw = -inf) and the largest exponent reached
+    # in a single late tile; a NaN in the last tile then gives PF_ERR_DOMAIN
+    if case == "gauss_2_6M":
+        lw = workloads.gaussian_logw(2_600_007, 2.0, seed=41)
+    elif case == "heavy_2e24":
+        lw = workloads.heavy_tail_logw(1 << 24, shift=10.0, frac=0.01, seed=3)
+    else:
+        lw = workloads.gaussian_logw(1 << 23, 1.0, seed=42)
+        lw[: 3 << 20] = -np.inf
+        lw[(5 << 20):(6 << 20)] = -np.inf
+        lw[(7 << 20) + 12345] = 40.0
+    e = torch.zeros(1, device="cuda")
+    ls = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pf.pf_ess(to_dev(lw), lw.size, e, ls)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    ess, log_sum = oracle.ess(lw)
+    assert e.item() == pytest.approx(ess, rel=2e-6)
+    assert ls.item() == pytest.approx(log_sum, rel=1e-12, abs=2e-6)
+    lw[lw.size - 7] = np.nan
+    pf.pf_ess(to_dev(lw), lw.size, e, ls)
+    assert pf.pf_get_device_status() == pf.PF_ERR_DOMAIN
+    assert np.isnan(e.item()) and np.isnan(ls.item())
+
+
 @pytest.mark.parametrize("row_bytes", [4, 12, 16, 64, 68, 256])
 @pytest.mark.parametrize("P", [1, 1000, 70001])
 def test_gather_bit_exact(row_bytes, P):
