@@ -160,7 +160,8 @@ def run_gpu(args):
                "inplace": lambda: run_inplace(args, pf, torch, dev),
                "sweep": lambda: run_size_sweep(args, pf, torch, dev, hbm_peak),
                "sorted": lambda: run_sorted_ablation(args, pf, torch, dev),
-               "phases": lambda: run_phases(args, pf, torch, dev, stream)}[args.only]()
+               "phases": lambda: run_phases(args, pf, torch, dev, stream),
+               "single": lambda: run_single(args, pf, torch, dev)}[args.only]()
         if rank == 0:
             print(json.dumps({"leg": args.only, **leg}))
         return
@@ -896,6 +897,47 @@ def run_inplace(args, pf, torch, dev):
     return {"workload": "P=2^20, states Px16 f32, systematic ancestors of N(0,s^2) log-weights", "rows": rows}
 
 
+def run_single(args, pf, torch, dev):
+    """One call kind at one size, `--reps` times (the first three untimed), L2
+    flushed before each: the command line the single-kernel ncu captures in
+    profiles/ use.  N(0,1) log-weights, states P x 16 f32 for the gather,
+    Metropolis B = 32."""
+    from paper_1202_6163_gb300 import workloads
+    s = torch.cuda.current_stream(dev)
+    stream = s.cuda_stream
+    P = args.P
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    pf.pf_reserve(P, 0, 0, stream)
+    lw = torch.from_numpy(workloads.gaussian_logw(P, SPREAD, seed=5)).to(dev)
+    anc = torch.empty(P, dtype=torch.int32, device=dev)
+    ess = torch.zeros(1, device=dev)
+    if args.kind == "gather":
+        st = torch.from_numpy(workloads.states(P, D_STATE, seed=6)).to(dev)
+        dst = torch.empty_like(st)
+        pf.pf_resample_systematic(lw, P, 0, 1, anc, stream)
+    calls = {"ess": lambda: pf.pf_ess(lw, P, ess, None, stream),
+             "systematic": lambda: pf.pf_resample_systematic(lw, P, 0, 1, anc, stream),
+             "stratified": lambda: pf.pf_resample_stratified(lw, P, 0, 1, anc, stream),
+             "multinomial": lambda: pf.pf_resample_multinomial(lw, P, 0, 1, anc, stream),
+             "metropolis": lambda: pf.pf_resample_metropolis(lw, P, METRO_B, 1, anc, stream),
+             "gather": lambda: pf.pf_gather(st, P, D_STATE * 4, anc, P, dst, stream)}
+    fn = calls[args.kind]
+    ts = []
+    for r in range(max(args.reps, 4)):
+        flush.zero_()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        z.record(s)
+        torch.cuda.synchronize(dev)
+        if r >= 3:
+            ts.append(a.elapsed_time(z) * 1e3)
+    if pf.pf_get_device_status(s) != pf.PF_OK:
+        raise RuntimeError("device status not OK")
+    return {"kind": args.kind, "P": P, "calls": len(ts) + 3, "median_us": round(statistics.median(ts), 2),
+            "l2": "flushed before each call"}
+
+
 def run_size_sweep(args, pf, torch, dev, hbm_peak):
     """Every single-filter call over P = 2^10 ... 2^24 (N(0,1) log-weights,
     states P x 16 for the gather): median time of 20 calls with L2 flushed
@@ -1256,9 +1298,12 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-figure2", action="store_true")
     ap.add_argument("--only", choices=["batched", "bootstrap", "figure2", "metropolis", "inplace", "sweep", "sorted",
-                                       "phases"],
+                                       "phases", "single"],
                     default=None,
                     help="run one secondary leg alone and print its JSON (for profiling)")
+    ap.add_argument("--kind", choices=["ess", "systematic", "stratified", "multinomial", "metropolis", "gather"],
+                    default="systematic", help="with --only single")
+    ap.add_argument("--reps", type=int, default=6, help="with --only single: calls, the first three untimed")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:

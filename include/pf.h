@@ -439,7 +439,8 @@ pf_status pf_debug_tile_weights(const float* logw, int64_t n, int k, float* weig
  * programs that forbid allocation after start-up.  It gives exactly the
  * ancestors pf_resample_multinomial gives (same random streams, same search
  * predicate), by the single-launch multinomial kernel with a plain binary
- * search per draw rather than the binned draws of pf_resample_multinomial, and
+ * search per draw rather than the windowed draws of pf_resample_multinomial
+ * (tile lookup, then 16-entry window reads of the cumulative weights), and
  * keeps its scratch in a fixed array compiled into the library:
  * PF_STATIC_MAX_PARTICLES floats of cumulative weights (4 MiB) plus 256 bytes of
  * control words and 16 KiB of tile records, present on every GPU that loads

@@ -9,9 +9,9 @@
 // synchronises the device) would stall a deadline, or builds that forbid
 // allocations once the application has started.  pf_resample_multinomial_static
 // runs the single-launch multinomial kernel with the plain binary search per
-// draw (not the binned draws of pf_resample_multinomial, whose bins would need
-// several times more scratch; both give the same ancestors) with its scratch in
-// the fixed array below.  The array belongs to the library's device code: CUDA
+// draw (not the windowed draws of pf_resample_multinomial, whose tile lookup and
+// strided samples of the cumulative weights would need more scratch; both give
+// the same ancestors) with its scratch in the fixed array below.  The array belongs to the library's device code: CUDA
 // loads that module on a device lazily, at the first call that needs it, so the
 // first call on each device (which also looks up the array's address) is the
 // one that may allocate or synchronise inside the driver, and should be made at
