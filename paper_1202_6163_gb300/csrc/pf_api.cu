@@ -273,7 +273,8 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     // every 16th (c2) and 256th (c1) for the three-level draws, when the c1
     // samples fit in shared memory beside the tile table
     int cpt2 = 0, cpt1 = 0, c1shift = 8;
-    size_t c2_at = 0, c1_at = 0, mscratch = 0;
+    size_t c2_at = 0, c1_at = 0, g_at = 0, mscratch = 0;
+    const int64_t M = (P + 3) / 4;  // multinomial guide buckets
     if (kind == PF_MULTINOMIAL) {
         // level-1 stride 2^c1shift >= 256: the smallest whose samples fit beside the table
         cpt2 = ((tile + 15) / 16 + 15) & ~15;
@@ -286,7 +287,8 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
             cpt1 = cpt2 = 0;
         c2_at = ((size_t)PA * sizeof(float) + 255) & ~(size_t)255;
         c1_at = (c2_at + (size_t)T * cpt2 * sizeof(float) + 255) & ~(size_t)255;
-        mscratch = c1_at + (size_t)T * cpt1 * sizeof(float);
+        g_at = (c1_at + (size_t)T * cpt1 * sizeof(float) + 255) & ~(size_t)255;
+        mscratch = cpt2 > 0 ? g_at + (size_t)M * sizeof(int32_t) : c1_at;
     } else if (R > 1) {
         mscratch = (size_t)PA * sizeof(float);  // cumulative weights of the tiles pass 2 reloads
     }
@@ -317,6 +319,12 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     p.c1shift = c1shift;
     p.trace = g_trace;
     p.trace_cap = g_trace_cap;
+    // the guide pays for its decode and second grid-wide wait only when each CTA
+    // draws for several tiles' worth of particles (P above one tile per resident
+    // CTA: 2^22 162 -> 122 us; at 2^20 it took 41.6 -> 45.7 us)
+    p.g_out = (cpt2 > 0 && R > 1) ? reinterpret_cast<int32_t*>((char*)w->scratch + g_at) : nullptr;
+    p.M = M;
+    p.guide = 0;
     return cuda_fail(launch_sorted_persistent(kind, p, G, s), "persistent launch");
 }
 
@@ -499,10 +507,12 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
     DeviceInfo* info;
     pf_status st = device_info(dev, info);
     if (st) return st;
-    // multinomial: P + 3 floats of cumulative weights and their 1/16 and 1/256 samples
+    // multinomial: P + 3 floats of cumulative weights, their 1/16 and 1/256 samples
+    // and the guide table of (P + 3) / 4 entries
     size_t need = (((size_t)(P_max + 3) * sizeof(float) + 255) & ~(size_t)255) +
                   (((size_t)(P_max + 3) / 16 + 16 * (size_t)kMaxTilesTotal) * sizeof(float) + 255) / 256 * 256 +
-                  ((size_t)(P_max + 3) / 256 + (size_t)kMaxTilesTotal) * sizeof(float);
+                  (((size_t)(P_max + 3) / 256 + (size_t)kMaxTilesTotal) * sizeof(float) + 255) / 256 * 256 +
+                  ((size_t)(P_max + 3) / 4 + 1) * sizeof(int32_t);
     const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
     if (red > need) need = red;
     if (F_max > 0) {

@@ -50,8 +50,9 @@ __device__ __forceinline__ long long offsets_below(const SortedParams& p, const 
     const fpair y = pair_mul(fixed_to_pair(B_i), PW);  // B P / W
     long long j;
     if (KIND == KIND_SYS) {
-        const u32x4 r = philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1);
-        const fpair d = pair_sub_f(y, u23f(r.x));
+        // the multinomial guide places its offsets at (j / P) W: no uniform shift
+        const float u = p.guide ? 0.f : u23f(philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1).x);
+        const fpair d = pair_sub_f(y, u);
         j = B_i <= 0 ? 0 : (B_i >= sm.Wt ? p.P : max(0LL, min((long long)p.P, pair_ceil(d))));
         x0 = __fadd_rn(__fsub_rn(d.hi, (float)j), d.lo);  // N(v) = ceil(v * inv_rho + x0)
     } else {
@@ -333,7 +334,12 @@ __device__ void assign_offspring(const SortedParams& p, AssignShared& sm, const 
         const int c1 = min(noff, c0 + kChunk);
         const int shift = (int)(((uintptr_t)(p.anc + jlo + c0) >> 2) & 3u);  // to a 16-byte boundary
         const int need = c1 - c0 + shift;
-        if (noff <= kChunk) {  // the tile's only chunk
+        if constexpr (CAP <= 4 * kThreads) {  // small staging (the multinomial guide): need <= CAP always
+            if (noff <= kChunk)
+                decode_chunk<4, KK, true>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
+            else
+                decode_chunk<4, KK>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
+        } else if (noff <= kChunk) {  // the tile's only chunk
             if (need <= 4 * kThreads)
                 decode_chunk<4, KK, true>(p, sm, out, th, jlo, c0, c1, shift, start0, tile_base, tag);
             else if (need <= 8 * kThreads)
@@ -728,6 +734,64 @@ __device__ __forceinline__ int32_t multinomial_draw_3level(uint32_t x, const Tab
         idx = w0 + below;
         if (below >= wn) idx = e.il;  // not reached: the window's last sample is above the target
         else if ((zmask >> below) & 1u) {  // rounding landed on a zero weight: the next positive one
+            int f = e.il;
+            for (int z = idx + 1; z < nt; ++z)
+                if (!zero_flag(__ldcg(v + b0 + z))) {
+                    f = z;
+                    break;
+                }
+            idx = f;
+        }
+    }
+    return (int32_t)(b0 + idx - lead);
+}
+
+// Single-launch multinomial draw through the guide table g[0..M): g[b] is the
+// first particle whose cumulative weight exceeds the bucket edge (b / M) W (the
+// systematic assignment's arithmetic with M offsets and no uniform shift).  A
+// draw whose uniform lies in bucket b = floor(u M) has its answer at or after
+// g[b], up to the rounding that separates the two arithmetics, so the draw
+// takes the tile holding particle g[b] - 1, confirms it with its own boundary
+// test (the tile's boundary at or below the target, the next one above it),
+// reads the 16-element window of v that starts at or just below g[b] - 1 and
+// counts the elements at or below its target.  That is the plain search's
+// result exactly when the window's first element is at or below the target (or
+// is the tile's first), and some element of the window is above it (or the
+// window ends the tile): the same predicate on the same monotone sequence.
+// Otherwise (a bucket holding more than ~12 particles, or an empty tile) ok is
+// false and the caller takes the three-level draw.  Every lane of the warp must
+// call it (quad-cooperative window read).
+__device__ __forceinline__ int32_t multinomial_draw_guided(uint32_t x, const TableEntry* table, int T,
+                                                           const float* v, const int32_t* g, int64_t M, int tile,
+                                                           int64_t PA, int lead, float Wh, float Wl, bool& ok) {
+    float uh, ul, th, tl;
+    u32_pair(x, uh, ul);
+    draw_target(uh, ul, Wh, Wl, th, tl);
+    // bucket of u = (2x + 1) 2^-33: floor(u M), exact in 64-bit integers
+    const int64_t b = (int64_t)(((2ull * x + 1ull) * (unsigned long long)M) >> 33);
+    int64_t h = (int64_t)__ldcg(g + b) - 1 + lead;  // aligned-window position of particle g[b] - 1
+    h = h < lead ? (int64_t)lead : (h > PA - 1 ? PA - 1 : h);
+    const int lo = (int)(h / tile);
+    const bool good = boundary_at_or_below(table[lo], th, tl) &&
+                      (lo + 1 >= T || !boundary_at_or_below(table[lo + 1], th, tl)) && table[lo].il >= 0;
+    const TableEntry e = table[lo];
+    float xh = __fmul_rn(__fsub_rn(th, e.bhi), e.sc);
+    float xl = __fmul_rn(__fsub_rn(tl, e.blo), e.sc);
+    if (xh + xl < 0.f) {
+        xh = 0.f;
+        xl = 0.f;
+    }
+    const int64_t b0 = (int64_t)lo * tile;
+    const int nt = (int)min((int64_t)tile, PA - b0);
+    const int w0 = (int)(h - b0) & ~3;
+    const int wn = good ? min(16, nt - w0) : 0;
+    uint32_t zmask;
+    const int below = quad_window_below<true>(v, (int)(b0 + w0), wn, xh, xl, zmask);
+    ok = good && (w0 == 0 || below >= 1) && (below < wn || w0 + wn >= nt);
+    int idx = e.il;
+    if (ok && below < wn) {
+        idx = w0 + below;
+        if ((zmask >> below) & 1u) {  // rounding landed on a zero weight: the next positive one
             int f = e.il;
             for (int z = idx + 1; z < nt; ++z)
                 if (!zero_flag(__ldcg(v + b0 + z))) {

@@ -81,6 +81,9 @@ __device__ __forceinline__ void filter_params(const BatchParams& bp, int f, int6
     p.c1_out = nullptr;
     p.cpt2 = p.cpt1 = 0;
     p.c1shift = 8;
+    p.g_out = nullptr;
+    p.M = 0;
+    p.guide = 0;
 }
 
 // Warp 0: the exact fixed-point carries of a filter's Tf tiles from their

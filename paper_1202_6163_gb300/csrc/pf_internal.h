@@ -31,6 +31,8 @@ enum : int {
     CTL_ARRIVE1 = 9,      //   used by alternate epochs (one is reset while the other counts)
     CTL_ITEMS = 10,       // work items of the current batched call (written by its plan pass)
     CTL_HEAVY = 11,       // batched Metropolis: filters on the list of shared (heavy) filters
+    CTL_ARRIVE2 = 12,     // second arrival counters of the single-launch multinomial kernel
+    CTL_ARRIVE3 = 13,     //   (after its guide table), alternating like CTL_ARRIVE0 / 1
     CTL_WORDS = 16
 };
 
@@ -70,6 +72,9 @@ struct SortedParams {
     int cpt2, cpt1, c1shift;
     uint64_t* trace;     // phase records (kTraceWords words each), or null
     int64_t trace_cap;   // records the trace buffer holds
+    int32_t* g_out;      // multinomial: the guide table g[M] (first particle above each bucket edge), or null
+    int64_t M;           // guide buckets
+    int guide;           // offsets at (j / P) W with no uniform shift (the guide's decode), else 0
 };
 
 // Batched call: F filters, filter f owns lw[offsets[f] .. offsets[f+1]).

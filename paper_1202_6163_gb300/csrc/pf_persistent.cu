@@ -45,8 +45,9 @@ struct PersistShared {
     TileShared tile;
     AssignShared as;
     i128 wsum[kWarps], wsum2[kWarps];
-    i128 Bown[kMaxOwn + 1];  // boundaries of this CTA's tiles (systematic, stratified)
-    // systematic / stratified: the owned tiles' summaries and offset maps
+    i128 Bown[kMaxOwn + 1];  // boundaries of this CTA's tiles
+    // the owned tiles' summaries and offset maps (multinomial: exponents, last
+    // positive elements and the guide's maps)
     TileMap own_map[kMaxOwn];
     float own_shi[kMaxOwn], own_slo[kMaxOwn];
     int own_k[kMaxOwn], own_il[kMaxOwn];
@@ -74,10 +75,12 @@ __host__ __device__ constexpr size_t persistent_smem_bytes(int kind, int T, int 
 // ---------------------------------------------------------------------------
 // Arrive on this epoch's counter with release semantics (after the CTA's
 // records are written) and wait, one thread, bounded, for every CTA.
+// `base` names the pair of counters (CTL_ARRIVE0, or CTL_ARRIVE2 for the
+// multinomial kernel's second arrival).
 __device__ bool arrive_and_wait(const SortedParams& p, PersistShared& sm, bool skip, uint32_t epoch,
-                                uint64_t t_start) {
+                                uint64_t t_start, int base = CTL_ARRIVE0) {
     const int tid = threadIdx.x;
-    uint32_t* arrive = p.ctl + CTL_ARRIVE0 + (epoch & 1u);
+    uint32_t* arrive = p.ctl + base + (epoch & 1u);
     if (tid == 0) {
         if (!skip) red_release_add_u32(arrive, 1u);
         int ok = 1;
@@ -151,15 +154,14 @@ __device__ bool carries(const SortedParams& p, PersistShared& sm, TableEntry* ta
             if (KIND == KIND_MULTI) {
                 const fpair b = fixed_to_pair(B);
                 table[t] = {b.hi, b.lo, pow2f(-sh), (int)r.w};
-            } else if (t >= t_first && t <= t_first + t_count) {
-                sm.Bown[t - t_first] = B;
             }
+            if (t >= t_first && t <= t_first + t_count) sm.Bown[t - t_first] = B;  // the owned tiles' boundaries
         }
     }
     if (tid == 0) {
         sm.as.K = K;
         sm.as.Wt = running;
-        if (KIND != KIND_MULTI && t_first + t_count == T) sm.Bown[t_count] = running;
+        if (t_first + t_count == T) sm.Bown[t_count] = running;
         const fpair Wp = fixed_to_pair(running);
         sm.as.W_hi = Wp.hi;
         sm.as.W_lo = Wp.lo;
@@ -296,6 +298,9 @@ __device__ bool carries_agg(const SortedParams& p, PersistShared& sm, int t_coun
 // ---------------------------------------------------------------------------
 // Multinomial draws (Figure 1a): binary searches in global units.
 // ---------------------------------------------------------------------------
+// GUIDE: draws through the guide table first (p.g_out set), else the
+// three-level search alone.
+template <bool GUIDE>
 __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, const TableEntry* table) {
     const int tid = threadIdx.x, cta = blockIdx.x, G = gridDim.x;
     const int T = p.n_tiles;
@@ -320,9 +325,22 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
         int32_t a[4];
         if (p.c2_out) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-                a[s] = multinomial_draw_3level(word_of(r, s), table, lut, T, p.v_out, p.c2_out, p.cpt2, c1, p.cpt1,
-                                               p.c1shift, p.tile, p.P + p.lead, p.lead, Wh, Wl);
+            for (int s = 0; s < 4; ++s) {
+                if (GUIDE) {
+                    bool ok;
+                    a[s] = multinomial_draw_guided(word_of(r, s), table, T, p.v_out, p.g_out, p.M, p.tile,
+                                                   p.P + p.lead, p.lead, Wh, Wl, ok);
+                    if (__any_sync(0xffffffffu, !ok)) {  // the three-level draw, for the lanes the guide did not settle
+                        const int32_t f = multinomial_draw_3level(word_of(r, s), table, lut, T, p.v_out, p.c2_out,
+                                                                  p.cpt2, c1, p.cpt1, p.c1shift, p.tile, p.P + p.lead,
+                                                                  p.lead, Wh, Wl);
+                        if (!ok) a[s] = f;
+                    }
+                } else {
+                    a[s] = multinomial_draw_3level(word_of(r, s), table, lut, T, p.v_out, p.c2_out, p.cpt2, c1,
+                                                   p.cpt1, p.c1shift, p.tile, p.P + p.lead, p.lead, Wh, Wl);
+                }
+            }
         } else {
             multinomial_draws4<false>(r, table, T, p.v_out, p.tile, p.P + p.lead, p.lead, Wh, Wl, a);
         }
@@ -337,8 +355,52 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Multinomial guide table (after the carries): g[b], b < M, the first particle
+// whose cumulative weight exceeds the bucket edge (b / M) W.  It is the
+// systematic assignment of M offsets at (j / M) W (no uniform shift) over the
+// owned tiles, decoded into g with its staging in the tile lookup's area (not
+// yet built); then a second grid-wide arrival, so that every entry is written
+// before any draw reads one.  Returns false when that wait ran out.
+// ---------------------------------------------------------------------------
+constexpr int kGuideCap = 2048;  // staging entries per buffer: offsets per chunk + room for the shift
+static_assert(2 * kGuideCap <= kLut + 1, "the guide's staging fits the tile lookup's area");
+
+template <int KK>
+__device__ bool build_guide(const SortedParams& p, PersistShared& sm, int32_t* stage, TileThread& th, TileSummary ts,
+                            int t_first, int t_count, uint32_t epoch, uint64_t t_start, bool skip) {
+    const int tid = threadIdx.x;
+    SortedParams pg = p;
+    pg.anc = p.g_out;
+    pg.P = p.M;
+    pg.Pd = (double)p.M;
+    pg.guide = 1;
+    stage_init<kGuideCap>(stage);
+    // the guide's offset map of every owned tile, two lanes per tile
+    if (tid < 2 * ((t_count + 15) & ~15)) {
+        const int r = min(tid >> 1, t_count - 1);
+        const TileMap m = tile_map_pair<KIND_SYS>(pg, sm.as, sm.Bown[r], sm.Bown[r + 1], sm.own_k[r], 0xffffffffu);
+        if ((tid & 1) == 0 && (tid >> 1) < t_count) sm.own_map[tid >> 1] = m;
+    }
+    __syncthreads();
+    const int64_t PA = p.P + p.lead;
+    uint32_t chunks = 0;
+    for (int r = t_count - 1; r >= 0; --r) {  // the last tile's scan is still in registers
+        const int64_t t0 = (int64_t)(t_first + r) * p.tile;
+        if (r != t_count - 1) {
+            read_tile_v<KK>(p.v_out + t0, (int)min((int64_t)p.tile, PA - t0), th);
+            ts.i_last = sm.own_il[r];
+        }
+        assign_offspring<KIND_SYS, KK, kGuideCap>(pg, sm.as, sm.own_map[r], stage, chunks, th, ts, t0 - p.lead);
+    }
+    __threadfence();
+    __syncthreads();
+    return arrive_and_wait(p, sm, skip, epoch, t_start, CTL_ARRIVE2);
+}
+
 // KK: elements per thread of a full tile (4, 8 or 16; the host picks it from p.tile).
-template <int KIND, int KK>
+// GUIDE (multinomial): draws through the guide table (p.g_out set).
+template <int KIND, int KK, bool GUIDE = false>
 __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PersistShared& sm = *reinterpret_cast<PersistShared*>(smem_raw);
@@ -418,9 +480,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
             if (p.c2_out)
                 write_tile_samples<KK>(th, n, p.c2_out + (int64_t)t * p.cpt2, p.c1_out + (int64_t)t * p.cpt1, p.c1shift);
             __threadfence();
-            if (tid == 0)
+            if (tid == 0) {
                 st_v4_u32(rec + 4 * t, (uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi),
                           __float_as_uint(ts.S.lo), (uint32_t)ts.i_last);
+                sm.own_k[r] = ts.k;
+                sm.own_il[r] = ts.i_last;
+            }
         } else {
             if (r + 1 < t_count) write_tile_v<KK>(p, th, t0, n);  // reloaded in pass 2
             if (tid == 0) {
@@ -455,12 +520,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     // advance the epoch
     if (blockIdx.x == 0 && tid == 0) {
         atomicExch(p.ctl + CTL_ARRIVE0 + ((epoch + 1u) & 1u), 0u);
+        if (KIND == KIND_MULTI) atomicExch(p.ctl + CTL_ARRIVE2 + ((epoch + 1u) & 1u), 0u);
         atomicExch(p.ctl + CTL_EPOCH, epoch);
     }
     if (!ok || !copy_ok) return;
 
     if (KIND == KIND_MULTI) {
-        multinomial_draws(p, sm, reinterpret_cast<const TableEntry*>(region));
+        if (GUIDE) {
+            int32_t* stage = reinterpret_cast<int32_t*>(region + (size_t)p.n_tiles * sizeof(TableEntry));
+            if (!build_guide<KK>(p, sm, stage, th, ts, t_first, t_count, epoch, t_start, skip)) {
+                if (tid == 0) set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
+                return;
+            }
+        }
+        multinomial_draws<GUIDE>(p, sm, reinterpret_cast<const TableEntry*>(region));
         if (p.trace) {
             __syncthreads();
             trace_stamp(p.trace, p.trace_cap, blockIdx.x, 4);
@@ -493,13 +566,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     }
 }
 
-template <int KIND, int KK>
+template <int KIND, int KK, bool GUIDE = false>
 static cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(k_persistent<KIND, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_persistent<KIND, KK, GUIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)persistent_smem_bytes(KIND, kMaxTilesTotal, KK));
 }
 
-template <int KIND, int KK>
+template <int KIND, int KK, bool GUIDE = false>
 static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -512,12 +585,17 @@ static cudaError_t launch_kind(const SortedParams& p, int grid, cudaStream_t s) 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_persistent<KIND, KK>, p);
+    return cudaLaunchKernelEx(&cfg, k_persistent<KIND, KK, GUIDE>, p);
 }
 
 template <int KIND>
 static cudaError_t launch_k(const SortedParams& p, int grid, cudaStream_t s) {
     const int q = (p.tile + kThreads - 1) / kThreads;  // elements per thread of a full tile
+    if (KIND == KIND_MULTI && p.g_out) {
+        if (q <= 4) return launch_kind<KIND, 4, true>(p, grid, s);
+        if (q <= 8) return launch_kind<KIND, 8, true>(p, grid, s);
+        return launch_kind<KIND, 16, true>(p, grid, s);
+    }
     if (q <= 4) return launch_kind<KIND, 4>(p, grid, s);
     if (q <= 8) return launch_kind<KIND, 8>(p, grid, s);
     return launch_kind<KIND, 16>(p, grid, s);
@@ -546,6 +624,15 @@ static int blocks_per_sm_kk() {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<KIND, KK>, kThreads,
                                                       persistent_smem_bytes(KIND, kMaxTilesTotal, KK)) != cudaSuccess)
         return 0;
+    if (KIND == KIND_MULTI) {  // the guide variant: the same launch shape, so the smaller of the two
+        int ng = 0;
+        if (set_smem_attr<KIND, KK, true>() != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ng, k_persistent<KIND, KK, true>, kThreads,
+                                                          persistent_smem_bytes(KIND, kMaxTilesTotal, KK)) !=
+                cudaSuccess)
+            return 0;
+        nb = min(nb, ng);
+    }
     return nb;
 }
 

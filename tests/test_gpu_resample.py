@@ -337,6 +337,40 @@ def test_cumulative_multi_tile_2_6M(kind):
     print(kind, "2.6M", rep.summary())
 
 
+@pytest.mark.parametrize("case", ["dead_runs", "one_heavy", "spread4", "ragged_unaligned"])
+def test_multinomial_guide_table_cases(case):
+    # above one tile per resident CTA the multinomial draws go through the guide
+    # table first: runs of zero-weight particles (whole tiles without mass, where
+    # the guide's tile has no positive element), a handful of particles holding
+    # almost all the weight (buckets spanning thousands of light particles, the
+    # three-level fallback), a wide spread, and a ragged unaligned view
+    rng = np.random.default_rng(31)
+    P = 3_000_017
+    lw = workloads.gaussian_logw(P, 1.0, seed=32)
+    if case == "dead_runs":
+        for start in rng.integers(0, P - 40000, size=12):
+            lw[start:start + int(rng.integers(100, 40000))] = -np.inf
+        lw[: 8192 * 3 + 5] = -np.inf
+    elif case == "one_heavy":
+        lw[rng.integers(0, P, size=7)] += 25.0
+    elif case == "spread4":
+        lw = workloads.gaussian_logw(P, 4.0, seed=33)
+    a_ref = oracle.multinomial(lw if case != "ragged_unaligned" else lw[3:], 41)
+    if case == "ragged_unaligned":
+        base = to_dev(lw)
+        view = base[3:]
+        a = torch.full((P - 3,), -7, dtype=torch.int32, device="cuda")
+        pf.pf_resample_multinomial(view, P - 3, 0, 41, a)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        rep = check_cumulative("multinomial", lw[3:], a.cpu().numpy(), a_ref, 41)
+    else:
+        a, st = gpu_resample(pf.pf_resample_multinomial, lw, 41)
+        assert st == pf.PF_OK
+        rep = check_cumulative("multinomial", lw, a, a_ref, 41)
+    assert rep.ok, rep.summary() + f" first failures: {rep.failures[:5]}"
+    print(case, rep.summary())
+
+
 @pytest.mark.parametrize("kind", list(CUMULATIVE))
 def test_cumulative_P2e24_heavy_tail(kind):
     # log-weights N(0,1) with 1% of entries shifted by +10
