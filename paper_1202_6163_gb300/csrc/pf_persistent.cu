@@ -347,10 +347,12 @@ __device__ void multinomial_draws(const SortedParams& p, PersistShared& sm, cons
         const int64_t j = 4 * q;
         if (!mine) continue;
         if (j + 3 < p.P && (((uintptr_t)(p.anc + j)) & 15u) == 0) {
-            *reinterpret_cast<int4*>(p.anc + j) = make_int4(a[0], a[1], a[2], a[3]);
+            // streaming store: the ancestors are not read again here, and evicting
+            // them first keeps L2 for the cumulative weights the draws read at random
+            __stcs(reinterpret_cast<int4*>(p.anc + j), make_int4(a[0], a[1], a[2], a[3]));
         } else {
             for (int s = 0; s < 4; ++s)
-                if (j + s < p.P) p.anc[j + s] = a[s];
+                if (j + s < p.P) __stcs(p.anc + j + s, a[s]);
         }
     }
 }
