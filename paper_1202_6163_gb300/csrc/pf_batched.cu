@@ -16,7 +16,11 @@
 //     assigns its own tile's offsets.  Tiles of one filter hold consecutive
 //     tickets and a filter has at most kMaxOwnB < grid tiles, so every tile a
 //     CTA waits for has been or will be taken by a running CTA (the launch is
-//     cooperative, so all CTAs are resident).
+//     cooperative, so all CTAs are resident);
+//   - unless such filters are at least as many as the resident CTAs: then the
+//     plan keeps each one whole, a single item whose CTA scans all its tiles
+//     (cumulative weights to the CTA's scratch), forms the carries and every
+//     tile's offset map, and assigns the tiles, with no wait on another CTA.
 // A filter's data may start at any 4-byte boundary: tiles are laid out on the
 // aligned window, with the leading slots taken as zero weights.  The last CTA
 // to finish resets the ticket; the last CTA of a split filter resets its

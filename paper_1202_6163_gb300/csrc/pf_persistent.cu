@@ -12,8 +12,9 @@
 //      (k_t, S_t, i_last);
 //   2. the CTA arrives on this launch's counter (release) and one thread waits,
 //      with a time limit, until every CTA has arrived;
-//   3. carries.  Systematic / stratified: warp 0 reads the G CTA records and
-//      forms the largest exponent K, the mass below this CTA and the total W
+//   3. carries.  Systematic / stratified: the CTA reads the G CTA records
+//      (one per thread) and forms the largest exponent K, the mass below this
+//      CTA and the total W
 //      = sum_c S_c 2^{k_c - K} (exact integer sums, so every CTA holds the
 //      same bits and W is the scan's own last prefix), then the boundaries of
 //      its own tiles from its own tile sums; two lanes per owned tile then
@@ -28,9 +29,14 @@
 //      weight, N_i, and its index fills [N_{i-1}, N_i) by a run-length decode
 //      in shared memory (mark run starts, block max-scan), stored with 128-bit
 //      writes;
-//      multinomial: the CTA draws a balanced slice of the P uniforms, finds the
-//      tile by a binary search over the boundaries and the element by a
-//      binary search in that tile's v_i.
+//      multinomial: the CTA draws a balanced slice of the P uniforms; a draw
+//      finds its tile from a lookup of the tile boundaries and its element in
+//      three levels (every 2^c1shift-th v_i in shared memory, then one
+//      16-entry window of the every-16th samples and one of v_i, read from L2).
+//      Above one tile per CTA the CTAs first decode a guide table (the first
+//      particle above each of P/4 evenly spaced targets) and arrive a second
+//      time; a draw then reads its guide entry and one window of v_i, and
+//      takes the three-level search only where that window does not settle it.
 // Every global write is bounded by [0, P) whatever the data; a NaN/+inf or
 // all-zero weight set records PF_ERR_DOMAIN and writes no ancestors.
 #include <climits>
