@@ -337,13 +337,16 @@ def test_cumulative_multi_tile_2_6M(kind):
     print(kind, "2.6M", rep.summary())
 
 
-@pytest.mark.parametrize("case", ["dead_runs", "one_heavy", "spread4", "ragged_unaligned"])
+@pytest.mark.parametrize("case", ["dead_runs", "one_heavy", "spread4", "ragged_unaligned", "dirichlet_0.01",
+                                  "equal_4M", "two_level"])
 def test_multinomial_guide_table_cases(case):
     # above one tile per resident CTA the multinomial draws go through the guide
     # table first: runs of zero-weight particles (whole tiles without mass, where
     # the guide's tile has no positive element), a handful of particles holding
     # almost all the weight (buckets spanning thousands of light particles, the
-    # three-level fallback), a wide spread, and a ragged unaligned view
+    # three-level fallback), a wide spread, a ragged unaligned view, the paper's
+    # Dirichlet law at alpha = .01, equal weights (every bucket exactly four
+    # particles) and alternating runs of heavy and light particles
     rng = np.random.default_rng(31)
     P = 3_000_017
     lw = workloads.gaussian_logw(P, 1.0, seed=32)
@@ -355,6 +358,13 @@ def test_multinomial_guide_table_cases(case):
         lw[rng.integers(0, P, size=7)] += 25.0
     elif case == "spread4":
         lw = workloads.gaussian_logw(P, 4.0, seed=33)
+    elif case == "dirichlet_0.01":  # the paper's weight law at its smallest alpha: log-weights spread over thousands
+        lw = workloads.dirichlet_logw(P, 0.01, seed=34)
+    elif case == "equal_4M":  # every bucket holds exactly four particles
+        P = 1 << 22
+        lw = np.full(P, -1.5, np.float32)
+    elif case == "two_level":  # alternating runs of heavy and light particles
+        lw = np.where((np.arange(P) // 1000) % 2 == 0, 3.0, -3.0).astype(np.float32)
     a_ref = oracle.multinomial(lw if case != "ragged_unaligned" else lw[3:], 41)
     if case == "ragged_unaligned":
         base = to_dev(lw)
