@@ -527,8 +527,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_persistent(SortedParams p) {
     // (or waited out its limit): reset the counter the next launch will use and
     // advance the epoch
     if (blockIdx.x == 0 && tid == 0) {
+        // every kind resets both pairs: the next launch on this stream, of whatever
+        // kind, may be a multinomial one that uses the second pair
         atomicExch(p.ctl + CTL_ARRIVE0 + ((epoch + 1u) & 1u), 0u);
-        if (KIND == KIND_MULTI) atomicExch(p.ctl + CTL_ARRIVE2 + ((epoch + 1u) & 1u), 0u);
+        atomicExch(p.ctl + CTL_ARRIVE2 + ((epoch + 1u) & 1u), 0u);
         atomicExch(p.ctl + CTL_EPOCH, epoch);
     }
     if (!ok || !copy_ok) return;

@@ -381,6 +381,23 @@ def test_multinomial_guide_table_cases(case):
     print(case, rep.summary())
 
 
+def test_multinomial_guide_after_other_kinds():
+    # the guide's second grid-wide arrival uses its own pair of epoch-alternating
+    # counters; every single-launch call resets the one the next call may use, so
+    # a guided multinomial call right after systematic or stratified calls (an odd
+    # or even number of them) still waits for every CTA's guide entries
+    P = 3_000_017
+    lw = workloads.gaussian_logw(P, 1.0, seed=36)
+    others = [pf.pf_resample_systematic, pf.pf_resample_stratified]
+    for gap in (0, 1, 2, 3, 4):
+        for k in range(gap):
+            gpu_resample(others[k % 2], lw, 50 + k)
+        a, st = gpu_resample(pf.pf_resample_multinomial, lw, 60 + gap)
+        assert st == pf.PF_OK
+        rep = check_cumulative("multinomial", lw, a, oracle.multinomial(lw, 60 + gap), 60 + gap)
+        assert rep.ok, (gap, rep.summary())
+
+
 @pytest.mark.parametrize("kind", list(CUMULATIVE))
 def test_cumulative_P2e24_heavy_tail(kind):
     # log-weights N(0,1) with 1% of entries shifted by +10
