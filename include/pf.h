@@ -84,7 +84,10 @@ enum {
     PF_METROPOLIS = 3
 };
 
-/* Largest P accepted by every call. */
+/* Largest P of the Metropolis, gather and ESS calls (int32 ancestors).  The
+ * systematic, stratified and multinomial single-filter calls stop at
+ * PF_MAX_CUMULATIVE and a filter of a batched cumulative call at
+ * PF_MAX_BATCHED_FILTER; beyond those they return PF_ERR_INVALID. */
 #define PF_MAX_PARTICLES 2147483647LL
 
 /* Largest P (plus the alignment lead of logw) of one single-filter systematic,
