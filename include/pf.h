@@ -84,14 +84,19 @@ enum {
     PF_METROPOLIS = 3
 };
 
-/* Largest P of the Metropolis, gather and ESS calls (int32 ancestors).  The
- * systematic, stratified and multinomial single-filter calls stop at
- * PF_MAX_CUMULATIVE and a filter of a batched cumulative call at
- * PF_MAX_BATCHED_FILTER; beyond those they return PF_ERR_INVALID. */
+/* Largest P of every single-filter call (int32 ancestors).  A filter of a
+ * batched cumulative call stops at PF_MAX_BATCHED_FILTER. */
 #define PF_MAX_PARTICLES 2147483647LL
 
-/* Largest P (plus the alignment lead of logw) of one single-filter systematic,
- * stratified or multinomial call: 4096 tiles of 8192 log-weights. */
+/* Largest P (plus the alignment lead of logw) that a single-filter
+ * systematic, stratified or multinomial call resamples in one cooperative
+ * launch (4096 tiles of 8192 log-weights).  Beyond it the call runs three
+ * ordinary launches on the stream -- the tile scans, one CTA forming every
+ * tile's exact carry, then the assignment (systematic, stratified: the tiles
+ * scanned again) or the draws (multinomial: plain binary searches over a tile
+ * table and the tiles' cumulative weights in global memory) -- with the same
+ * tiles, boundaries and per-tile arithmetic, and workspace scratch of about
+ * 48 bytes per 8192 particles (multinomial: 4 bytes per particle more). */
 #define PF_MAX_CUMULATIVE (1LL << 25)
 
 /* Largest P_f (plus the alignment lead) of one filter in a batched
@@ -104,15 +109,17 @@ enum {
  * c_i > (j + u) W / P, j = 0..P-1.  Output is non-decreasing and every
  * particle gets floor(P w_i/W) or ceil(P w_i/W) offspring.
  *   logw      [P] float, 4-byte aligned       (in)
- *   P         1 <= P and P + ((logw mod 16) / 4) <= PF_MAX_CUMULATIVE
+ *   P         1 <= P <= PF_MAX_PARTICLES
  *   B         ignored
  *   seed      Philox key
  *   ancestors [P] int32, 4-byte aligned       (out)
- * One cooperative launch: every CTA scans its tiles, publishes one record per
- * tile, waits (bounded) for all records, forms its carries and assigns its
- * ancestors.  Errors: PF_ERR_INVALID for null or misaligned pointers or P out
- * of range; device status PF_ERR_DOMAIN for NaN/+inf or all -inf log-weights,
- * PF_ERR_TIMEOUT if the wait for the other CTAs' records ran out.
+ * One cooperative launch while P + ((logw mod 16) / 4) <= PF_MAX_CUMULATIVE:
+ * every CTA scans its tiles, publishes one record for them, waits (bounded)
+ * for all records, forms its carries and assigns its ancestors; larger P as
+ * PF_MAX_CUMULATIVE describes.  Errors: PF_ERR_INVALID for null or misaligned
+ * pointers or P out of range; device status PF_ERR_DOMAIN for NaN/+inf or all
+ * -inf log-weights, PF_ERR_TIMEOUT if the wait for the other CTAs' records ran
+ * out.
  */
 pf_status pf_resample_systematic(const float* logw, int64_t P, int B, uint64_t seed,
                                  int32_t* ancestors, void* stream);

@@ -19,6 +19,9 @@ namespace pf {
 cudaError_t launch_metropolis(const float* lw, int64_t P, int B, const uint32_t* B_dev, uint32_t key0, uint32_t key1,
                               uint32_t filter, int32_t* anc, uint32_t* ctl, int num_sms, cudaStream_t s, int rounds);
 cudaError_t prepare_metropolis();
+cudaError_t prepare_large();
+cudaError_t launch_large(int kind, SortedParams p, void* scratch, int num_sms, cudaStream_t s);
+size_t large_scratch_bytes(int kind, int64_t PA);
 cudaError_t launch_gather(const void* src, int64_t P_src, int64_t row_bytes, const int32_t* anc, int64_t P_dst,
                           void* dst, uint32_t* ctl, int num_sms, cudaStream_t s);
 cudaError_t launch_reduce(const float* lw, int64_t P, void* rec, uint32_t* ctl, float* ess_out, double* log_sum_out,
@@ -96,6 +99,8 @@ pf_status device_info(int& dev, DeviceInfo*& info) {
     info->batched_per_sm[PF_METROPOLIS] = batched_metropolis_blocks_per_sm();
     e = prepare_metropolis();
     if (e != cudaSuccess) return cuda_fail(e, "prepare_metropolis");
+    e = prepare_large();
+    if (e != cudaSuccess) return cuda_fail(e, "prepare_large");
     info->ready = true;
     return PF_OK;
 }
@@ -255,13 +260,33 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     // tiles are laid out on the 16-byte aligned window that starts `lead` floats before logw
     const int lead = (int)(((uintptr_t)logw >> 2) & 3u);
     const int64_t PA = P + lead;
-    if (PA > PF_MAX_CUMULATIVE) return PF_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
     DeviceInfo* info;
     pf_status st = device_info(dev, info);
     if (st) return st;
+    if (PA > PF_MAX_CUMULATIVE) {
+        // beyond one cooperative launch's tiles: three ordinary launches (pf_large.cu)
+        Workspace* w;
+        st = workspace(s, large_scratch_bytes(kind, PA), w);
+        if (st) return st;
+        SortedParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.lw = logw - lead;
+        p.anc = anc;
+        p.lead = lead;
+        p.P = P;
+        p.Pd = (double)P;
+        p.key0 = (uint32_t)(seed & 0xffffffffu);
+        p.key1 = (uint32_t)(seed >> 32);
+        p.filter = 0;
+        p.ctl = w->ctl;
+        p.slots = w->slots;
+        p.wait_ns = g_wait_ns;
+        p.skip_tile = -1;
+        return cuda_fail(launch_large(kind, p, w->scratch, info->num_sms, s), "large launch");
+    }
     int G, tile, T, R;
     // at most one CTA per thread of a CTA: the carries read one CTA record per thread
     const int G_max = std::min(info->num_sms * info->persist_per_sm[kind], kThreads);
@@ -515,6 +540,10 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
                   ((size_t)(P_max + 3) / 4 + 1) * sizeof(int32_t);
     const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
     if (red > need) need = red;
+    if (P_max + 3 > PF_MAX_CUMULATIVE) {  // the three-launch path of larger single filters
+        const size_t large = large_scratch_bytes(PF_MULTINOMIAL, P_max + 3);
+        if (large > need) need = large;
+    }
     if (F_max > 0) {
         for (int k = PF_MULTINOMIAL; k <= PF_METROPOLIS; ++k) {
             const size_t per_cta = k != PF_METROPOLIS ? batched_scratch_floats_per_cta() : 0;

@@ -38,12 +38,19 @@ struct AssignShared {
 // ---------------------------------------------------------------------------
 // Per-tile scalars (lanes 0 and 1 of warp 0), in float pairs: the tile's
 // offset range and the map from tile-local cumulative weight v to the offset
-// coordinate y = v * inv_rho + x0 (offsets counted from jlo).  P <= 2^25 on
-// this path.
+// coordinate y = v * inv_rho + x0 (offsets counted from jlo).
 // One end of a tile's offset range: the offsets below boundary B (B_t for
 // the lower end, B_{t+1} for the upper), the same function of B for both, so
 // adjacent tiles share their common end exactly.  A boundary at 0 gives 0 and
 // one at the total mass W gives P.  Lower end (SYS, STRAT): x0 of the map.
+// (a.hi - j) + a.lo for an integer j near a.hi: the subtraction is exact even
+// where j has no float representation (odd j above 2^24, with P up to 2^31),
+// as a small integer plus the exact fraction of a.hi.
+__device__ __forceinline__ float pair_minus_int(fpair a, long long j) {
+    const float fh = floorf(a.hi);
+    return __fadd_rn(__fadd_rn((float)((long long)fh - j), __fsub_rn(a.hi, fh)), a.lo);
+}
+
 template <int KIND>
 __device__ __forceinline__ long long offsets_below(const SortedParams& p, const AssignShared& sm, fpair PW, i128 B_i,
                                                    float& x0) {
@@ -54,7 +61,7 @@ __device__ __forceinline__ long long offsets_below(const SortedParams& p, const 
         const float u = p.guide ? 0.f : u23f(philox(0u, 0u, p.filter, TAG_SYS, p.key0, p.key1).x);
         const fpair d = pair_sub_f(y, u);
         j = B_i <= 0 ? 0 : (B_i >= sm.Wt ? p.P : max(0LL, min((long long)p.P, pair_ceil(d))));
-        x0 = __fadd_rn(__fsub_rn(d.hi, (float)j), d.lo);  // N(v) = ceil(v * inv_rho + x0)
+        x0 = pair_minus_int(d, j);  // N(v) = ceil(v * inv_rho + x0)
     } else {
         j = 0;
         if (B_i >= sm.Wt) {
@@ -64,12 +71,12 @@ __device__ __forceinline__ long long offsets_below(const SortedParams& p, const 
             if (f >= p.P) {
                 j = p.P;
             } else {
-                const float frac = __fadd_rn(__fsub_rn(y.hi, (float)f), y.lo);
+                const float frac = pair_minus_int(y, f);
                 const u32x4 r = philox((uint32_t)(f >> 2), 0u, p.filter, TAG_STRAT, p.key0, p.key1);
                 j = max(0LL, f + (u23f(word_of(r, (int)(f & 3))) < frac ? 1 : 0));
             }
         }
-        x0 = __fadd_rn(__fsub_rn(y.hi, (float)j), y.lo);  // y(v) = v * inv_rho + x0
+        x0 = pair_minus_int(y, j);  // y(v) = v * inv_rho + x0
     }
     return j;
 }

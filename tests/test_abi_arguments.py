@@ -38,9 +38,6 @@ CHILD = textwrap.dedent(r"""
         add(fn, A, (1 << 31), 0, 1, B_, None)        # P > PF_MAX_PARTICLES
         add(fn, A + 2, 1024, 0, 1, B_, None)         # logw not 4-byte aligned
         add(fn, A, 1024, 0, 1, B_ + 1, None)         # ancestors not 4-byte aligned
-    for fn in ("pf_resample_systematic", "pf_resample_stratified", "pf_resample_multinomial"):
-        add(fn, A, MAXC + 1, 0, 1, B_ + (1 << 28), None)   # P beyond one call's tiles
-        add(fn, A + 4, MAXC, 0, 1, B_ + (1 << 28), None)   # P + lead beyond them
     add("pf_resample_metropolis", A + 4, 1024, -1, 1, B_, None)   # B < 0 needs 16-byte logw
 
     add("pf_gather", None, 16, 4, A, 16, B_, None)    # null src
@@ -139,7 +136,10 @@ CHILD = textwrap.dedent(r"""
     wf = [int(lib.pf_resample_systematic(A, 1024, 0, 1, B_, None)),
           int(lib.pf_ess(A, 1024, B_, None, None)),
           int(lib.pf_get_min_tile(pf.PF_METROPOLIS, 1024))]
-    print(json.dumps({"invalid": out, "well_formed": wf}))
+    # beyond one cooperative launch's tiles the cumulative calls are well formed too
+    wf_large = [int(getattr(lib, fn)(A + 4, MAXC, 0, 1, B_ + (1 << 28), None))
+                for fn in ("pf_resample_systematic", "pf_resample_stratified", "pf_resample_multinomial")]
+    print(json.dumps({"invalid": out, "well_formed": wf, "well_formed_large": wf_large}))
 """)
 
 
@@ -168,3 +168,4 @@ def test_well_formed_calls_reach_the_device_query(child_result):
     st_sys, st_ess, min_tile = child_result["well_formed"]
     assert st_sys == 4 and st_ess == 4      # PF_ERR_CUDA: no device visible
     assert min_tile == -1                   # Metropolis has no tile setting
+    assert child_result["well_formed_large"] == [4, 4, 4]  # P + lead beyond PF_MAX_CUMULATIVE: accepted

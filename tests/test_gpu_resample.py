@@ -381,6 +381,50 @@ def test_multinomial_guide_table_cases(case):
     print(case, rep.summary())
 
 
+@pytest.mark.parametrize("kind", ["systematic", "stratified"])
+def test_offsets_beyond_2e24_in_one_launch(kind):
+    # 2^24 < P <= 2^25 in the single cooperative launch: offset counts above 2^24
+    # have no exact float, so each tile's offset map takes its origin from the
+    # exact pair minus the integer count; the mismatches stay rare near ties
+    P = (1 << 24) + (1 << 23) + 5
+    lw = workloads.gaussian_logw(P, 1.0, seed=93)
+    rep = assert_cumulative(kind, lw, seed=21)
+    assert rep.mismatches <= P // 1000, rep.summary()
+    print(kind, "2^24 + 2^23 + 5", rep.summary())
+
+
+@pytest.mark.parametrize("kind", list(CUMULATIVE))
+def test_cumulative_beyond_one_launch(kind):
+    # P + lead above 4096 tiles of 8192: the tile scans, one CTA forming every
+    # tile's carry, then the assignment or the draws, as three ordinary launches
+    P = (1 << 25) + 12345
+    lw = workloads.gaussian_logw(P, 1.0, seed=91)
+    rep = assert_cumulative(kind, lw, seed=13)
+    assert rep.mismatches <= P // 1000, rep.summary()
+    print(kind, "2^25 + 12345", rep.summary())
+
+
+def test_cumulative_beyond_one_launch_unaligned_heavy_tail_and_errors():
+    P = (1 << 25) + 3
+    lw = workloads.heavy_tail_logw(P + 1, shift=10.0, frac=0.01, seed=92)
+    base = to_dev(lw)
+    view = base[1:]  # a lead of one float: P + lead = 2^25 + 4
+    for kind, (fn, orc) in CUMULATIVE.items():
+        a = torch.full((P,), -7, dtype=torch.int32, device="cuda")
+        fn(view, P, 0, 17, a)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        rep = check_cumulative(kind, lw[1:], a.cpu().numpy(), orc(lw[1:], 17), 17)
+        assert rep.ok, (kind, rep.summary())
+    bad = lw[1:].copy()
+    bad[P - 2] = np.nan
+    zero = np.full(P, -np.inf, np.float32)
+    for arr in (bad, zero):
+        for kind, (fn, _) in CUMULATIVE.items():
+            a, st = gpu_resample(fn, arr, 3)
+            assert st == pf.PF_ERR_DOMAIN, kind
+            assert np.all(a == -7), kind  # no ancestor written
+
+
 def test_multinomial_guide_after_other_kinds():
     # the guide's second grid-wide arrival uses its own pair of epoch-alternating
     # counters; every single-launch call resets the one the next call may use, so
