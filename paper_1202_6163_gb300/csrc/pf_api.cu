@@ -266,11 +266,11 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
     DeviceInfo* info;
     pf_status st = device_info(dev, info);
     if (st) return st;
-    if (PA > PF_MAX_CUMULATIVE) {
-        // beyond one cooperative launch's tiles: three ordinary launches (pf_large.cu)
+    // beyond one cooperative launch's tiles: ordinary launches in sequence (pf_large.cu)
+    auto run_large = [&]() -> pf_status {
         Workspace* w;
-        st = workspace(s, large_scratch_bytes(kind, PA), w);
-        if (st) return st;
+        pf_status sl = workspace(s, large_scratch_bytes(kind, PA), w);
+        if (sl) return sl;
         SortedParams p;
         std::memset(&p, 0, sizeof(p));
         p.lw = logw - lead;
@@ -286,7 +286,8 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
         p.wait_ns = g_wait_ns;
         p.skip_tile = -1;
         return cuda_fail(launch_large(kind, p, w->scratch, info->num_sms, s), "large launch");
-    }
+    };
+    if (PA > PF_MAX_CUMULATIVE) return run_large();
     int G, tile, T, R;
     // at most one CTA per thread of a CTA: the carries read one CTA record per thread
     const int G_max = std::min(info->num_sms * info->persist_per_sm[kind], kThreads);
@@ -308,8 +309,10 @@ pf_status resample_cumulative(int kind, const float* logw, int64_t P, uint64_t s
                    (size_t)kMaxTilesTotal * sizeof(float4))
             ++c1shift;
         cpt1 = (tile + (1 << c1shift) - 1) >> c1shift;
+        // the level-1 samples of this many tiles do not fit beside the table: the
+        // ordinary launches' guide table serves such P better than plain searches
         if ((size_t)T * sizeof(float4) + (size_t)T * cpt1 * sizeof(float) > (size_t)kMaxTilesTotal * sizeof(float4))
-            cpt1 = cpt2 = 0;
+            return run_large();
         c2_at = ((size_t)PA * sizeof(float) + 255) & ~(size_t)255;
         c1_at = (c2_at + (size_t)T * cpt2 * sizeof(float) + 255) & ~(size_t)255;
         g_at = (c1_at + (size_t)T * cpt1 * sizeof(float) + 255) & ~(size_t)255;
@@ -540,7 +543,7 @@ pf_status pf_reserve(int64_t P_max, int64_t total_max, int F_max, void* stream) 
                   ((size_t)(P_max + 3) / 4 + 1) * sizeof(int32_t);
     const size_t red = reduce_scratch(P_max > 0 ? P_max : 1);
     if (red > need) need = red;
-    if (P_max + 3 > PF_MAX_CUMULATIVE) {  // the three-launch path of larger single filters
+    if (P_max + 3 > ((int64_t)1 << 24)) {  // the ordinary-launch path of large single filters
         const size_t large = large_scratch_bytes(PF_MULTINOMIAL, P_max + 3);
         if (large > need) need = large;
     }

@@ -11,9 +11,11 @@
 //      block scan of the run totals), W = B_T, and the multinomial's tile table;
 //   3. k_large_assign (systematic, stratified): grid-stride over tiles: the
 //      tile scan again, the tile's offset map from B_t and B_{t+1}, the offsets
-//      and their run-length decode (pf_assign.cuh); k_large_draws
-//      (multinomial): grid-stride over Philox blocks, each draw a binary search
-//      over the tile table in global memory, then in its tile's v_i.
+//      and their run-length decode (pf_assign.cuh).  Multinomial: k_large_guide
+//      decodes the guide table (the first particle above each of P/4 evenly
+//      spaced targets) from the stored v_i, then k_large_draws runs the draws,
+//      each through its guide entry and one window of v_i, or, where that does
+//      not settle it, by binary searches over the tile table and the tile's v_i.
 // The tiles, the exact boundaries and the per-tile arithmetic are those of the
 // single-launch kernels, so the results follow the same rules.  A NaN/+inf or
 // all-zero weight set records PF_ERR_DOMAIN in launch 1 or 2, and launch 3
@@ -195,20 +197,86 @@ __global__ void __launch_bounds__(kThreads, 2) k_large_assign(SortedParams p, co
 }
 
 // ---------------------------------------------------------------------------
+// Multinomial, between launches 2 and 3: the guide table g[b], b < M = P / 4,
+// the first particle whose cumulative weight exceeds the bucket edge
+// (b / M) W -- the systematic assignment of M offsets with no uniform shift,
+// from each tile's stored cumulative weights (pg: the call's parameters with
+// anc = g, P = M, guide = 1; PA the call's P + lead).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 2) k_large_guide(SortedParams pg, int64_t PA, const uint4* rec,
+                                                             const i128* bnd, const LargeScalars* sc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LargeShared& sm = *reinterpret_cast<LargeShared*>(smem_raw);
+    int32_t* stage = reinterpret_cast<int32_t*>(smem_raw + sizeof(LargeShared));
+    const int tid = threadIdx.x;
+    if (!sc->ok) return;
+    if (tid == 0) {
+        sm.as.Wt = sc->Wt;
+        sm.as.K = sc->K;
+        sm.as.W_hi = sc->W_hi;
+        sm.as.W_lo = sc->W_lo;
+    }
+    stage_init<kIoCap>(stage);
+    __syncthreads();
+    uint32_t chunks = 0;
+    TileThread th;
+    for (int t = blockIdx.x; t < pg.n_tiles; t += gridDim.x) {
+        const int64_t t0 = (int64_t)t * kLargeTile;
+        const int n = (int)min((int64_t)kLargeTile, PA - t0);
+        read_tile_v<16>(pg.v_out + t0, n, th);
+        const uint4 r = rec[t];
+        TileSummary ts;
+        ts.k = (int)r.x;
+        ts.i_last = (int)r.w;
+        ts.bad = 0;
+        ts.S = {__uint_as_float(r.y), __uint_as_float(r.z)};
+        if (tid < 32) {
+            const TileMap m = tile_map_pair<KIND_SYS>(pg, sm.as, bnd[t], bnd[t + 1], ts.k, 0xffffffffu);
+            if (tid == 0) sm.map = m;
+        }
+        __syncthreads();
+        assign_offspring<KIND_SYS, 16, kIoCap>(pg, sm.as, sm.map, stage, chunks, th, ts, t0 - pg.lead);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launch 3, multinomial: every draw searches the tile table, then its tile's
 // cumulative weights (the plain binary searches of Section 2's description,
 // through L2).
 // ---------------------------------------------------------------------------
+// GUIDE: each draw first reads its guide entry and one 16-element window of v
+// (quad-cooperatively, pf_assign.cuh); a lane whose four draws the guide did
+// not all settle redoes its Philox block by the plain searches (same results).
+template <bool GUIDE>
 __global__ void __launch_bounds__(kThreads, 2) k_large_draws(SortedParams p, const TableEntry* table,
-                                                             const LargeScalars* sc) {
+                                                             const LargeScalars* sc, const int32_t* g, int64_t M) {
     if (!sc->ok) return;
     const float Wh = sc->W_hi, Wl = sc->W_lo;
     const int64_t PA = p.P + p.lead;
     const int64_t nq = (p.P + 3) >> 2;  // four draws per Philox block
-    for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < nq; q += (int64_t)gridDim.x * kThreads) {
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    // the same number of passes in every thread of a CTA (the guided draws read their
+    // windows quad-cooperatively); a lane past the end redraws block 0 and stores nothing
+    for (int64_t q0 = (int64_t)blockIdx.x * kThreads; q0 < nq; q0 += stride) {
+        const bool mine = q0 + threadIdx.x < nq;
+        if (!__any_sync(0xffffffffu, mine)) continue;  // the whole warp is past the end
+        const int64_t q = mine ? q0 + threadIdx.x : 0;
         const u32x4 r = philox((uint32_t)q, 0u, p.filter, TAG_MULTI, p.key0, p.key1);
         int32_t a[4];
-        multinomial_draws4<false>(r, table, p.n_tiles, p.v_out, kLargeTile, PA, p.lead, Wh, Wl, a);
+        bool settled = false;
+        if (GUIDE) {
+            settled = true;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                bool ok;
+                a[s] = multinomial_draw_guided(word_of(r, s), table, p.n_tiles, p.v_out, g, M, kLargeTile, PA,
+                                               p.lead, Wh, Wl, ok);
+                settled = settled && ok;
+            }
+        }
+        if (!settled) multinomial_draws4<false>(r, table, p.n_tiles, p.v_out, kLargeTile, PA, p.lead, Wh, Wl, a);
+        if (!mine) continue;
         const int64_t j = 4 * q;
         if (j + 3 < p.P && (((uintptr_t)(p.anc + j)) & 15u) == 0) {
             __stcs(reinterpret_cast<int4*>(p.anc + j), make_int4(a[0], a[1], a[2], a[3]));
@@ -225,18 +293,23 @@ namespace {
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct LargeLayout {
-    size_t rec, bnd, table, scalars, v, total;
+    size_t rec, bnd, table, scalars, v, g, total;
 };
+
+// Multinomial guide buckets: a quarter of the particles.
+int64_t guide_buckets(int64_t P) { return (P + 3) / 4; }
 
 LargeLayout large_layout(int kind, int64_t PA) {
     const size_t T = (size_t)((PA + kLargeTile - 1) / kLargeTile);
+    const bool multi = kind == KIND_MULTI;
     LargeLayout l;
     l.rec = 0;
     l.bnd = align256(T * sizeof(uint4));
     l.table = align256(l.bnd + (T + 1) * sizeof(i128));
-    l.scalars = align256(l.table + (kind == KIND_MULTI ? T * sizeof(TableEntry) : 0));
+    l.scalars = align256(l.table + (multi ? T * sizeof(TableEntry) : 0));
     l.v = align256(l.scalars + sizeof(LargeScalars));
-    l.total = l.v + (kind == KIND_MULTI ? (size_t)PA * sizeof(float) : 0);
+    l.g = align256(l.v + (multi ? (size_t)PA * sizeof(float) : 0));
+    l.total = l.g + (multi ? (size_t)guide_buckets(PA) * sizeof(int32_t) : 0);
     return l;
 }
 
@@ -260,10 +333,21 @@ cudaError_t launch_large_kind(SortedParams p, unsigned char* scratch, int num_sm
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if constexpr (KIND == KIND_MULTI) {
+        // the guide table, then the draws through it
+        int32_t* g = reinterpret_cast<int32_t*>(scratch + l.g);
+        const int64_t M = guide_buckets(p.P);
+        SortedParams pg = p;
+        pg.anc = g;
+        pg.P = M;
+        pg.Pd = (double)M;
+        pg.guide = 1;
+        k_large_guide<<<grid, kThreads, kAssignSmem, s>>>(pg, PA, rec, bnd, sc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         const int64_t nq = (p.P + 3) >> 2;
-        int64_t g = (nq + kThreads - 1) / kThreads;
-        if (g > (int64_t)num_sms * 16) g = (int64_t)num_sms * 16;
-        k_large_draws<<<(unsigned)g, kThreads, 0, s>>>(p, table, sc);
+        int64_t gd = (nq + kThreads - 1) / kThreads;
+        if (gd > (int64_t)num_sms * 16) gd = (int64_t)num_sms * 16;
+        k_large_draws<true><<<(unsigned)gd, kThreads, 0, s>>>(p, table, sc, g, M);
     } else {
         k_large_assign<KIND><<<grid, kThreads, kAssignSmem, s>>>(p, bnd, sc);
     }
@@ -279,6 +363,8 @@ cudaError_t prepare_large() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_large_assign<KIND_STRAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kAssignSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_large_guide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAssignSmem);
     return e;
 }
 

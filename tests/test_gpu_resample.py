@@ -381,7 +381,7 @@ def test_multinomial_guide_table_cases(case):
     print(case, rep.summary())
 
 
-@pytest.mark.parametrize("kind", ["systematic", "stratified"])
+@pytest.mark.parametrize("kind", list(CUMULATIVE))
 def test_offsets_beyond_2e24_in_one_launch(kind):
     # 2^24 < P <= 2^25 in the single cooperative launch: offset counts above 2^24
     # have no exact float, so each tile's offset map takes its origin from the
@@ -402,6 +402,17 @@ def test_cumulative_beyond_one_launch(kind):
     rep = assert_cumulative(kind, lw, seed=13)
     assert rep.mismatches <= P // 1000, rep.summary()
     print(kind, "2^25 + 12345", rep.summary())
+
+
+def test_multinomial_ordinary_launches_below_the_tile_limit():
+    # 3400 tiles of 8192: the tile table and its level-1 samples no longer fit
+    # shared memory, so the multinomial takes the ordinary launches and their
+    # guide table although one cooperative launch could hold the tiles
+    P = 3400 * 8192 - 11
+    lw = workloads.gaussian_logw(P, 2.0, seed=94)
+    rep = assert_cumulative("multinomial", lw, seed=23)
+    assert rep.mismatches <= P // 1000, rep.summary()
+    print("multinomial", P, rep.summary())
 
 
 def test_cumulative_beyond_one_launch_unaligned_heavy_tail_and_errors():
