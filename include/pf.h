@@ -93,10 +93,13 @@ enum {
  * launch (4096 tiles of 8192 log-weights).  Beyond it the call runs three
  * ordinary launches on the stream -- the tile scans, one CTA forming every
  * tile's exact carry, then the assignment (systematic, stratified: the tiles
- * scanned again) or the draws (multinomial: plain binary searches over a tile
- * table and the tiles' cumulative weights in global memory) -- with the same
+ * scanned again) or, for the multinomial, a guide table and the draws (each
+ * through its guide entry and one window of the stored cumulative weights,
+ * else binary searches over the tile table and the tile) -- with the same
  * tiles, boundaries and per-tile arithmetic, and workspace scratch of about
- * 48 bytes per 8192 particles (multinomial: 4 bytes per particle more). */
+ * 48 bytes per 8192 particles (multinomial: 5 bytes per particle more).  A
+ * multinomial call also takes these launches from about 3300 tiles on, where
+ * its tile table and samples no longer fit shared memory. */
 #define PF_MAX_CUMULATIVE (1LL << 25)
 
 /* Largest P_f (plus the alignment lead) of one filter in a batched
