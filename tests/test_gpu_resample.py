@@ -502,12 +502,24 @@ def test_config3_P2e24_metropolis_autotuned_B_and_gather():
                                   st[torch.from_numpy(a[rows]).long().cuda()].cpu().numpy())
 
 
-def test_cumulative_beyond_single_launch_capacity_is_rejected():
+def test_cumulative_one_past_single_launch_capacity_is_served():
+    # one particle past 4096 tiles of 8192: the ordinary launches, with equal
+    # weights every particle keeps one offspring (systematic, stratified), and
+    # P beyond PF_MAX_PARTICLES is still rejected on the host
     P = (1 << 25) + 1
     t = torch.zeros(P, device="cuda")
-    a = torch.zeros(P, dtype=torch.int32, device="cuda")
+    for fn in (pf.pf_resample_systematic, pf.pf_resample_stratified):
+        a = torch.full((P,), -7, dtype=torch.int32, device="cuda")
+        fn(t, P, 0, 0, a)
+        assert pf.pf_get_device_status() == pf.PF_OK
+        counts = torch.bincount(a.long(), minlength=P)
+        assert counts.numel() == P and int((counts != 1).sum()) <= P // 1000
+    a = torch.full((P,), -7, dtype=torch.int32, device="cuda")
+    pf.pf_resample_multinomial(t, P, 0, 0, a)
+    assert pf.pf_get_device_status() == pf.PF_OK
+    assert int(a.min()) >= 0 and int(a.max()) < P
     with pytest.raises(pf.PFError) as ei:
-        pf.pf_resample_systematic(t, P, 0, 0, a)
+        pf.pf_resample_systematic(t, 1 << 31, 0, 0, a)
     assert ei.value.status == pf.PF_ERR_INVALID
 
 
