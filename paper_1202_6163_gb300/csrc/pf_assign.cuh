@@ -778,7 +778,8 @@ __device__ __forceinline__ int32_t multinomial_draw_guided(uint32_t x, const Tab
     const int64_t b = (int64_t)(((2ull * x + 1ull) * (unsigned long long)M) >> 33);
     int64_t h = (int64_t)__ldcg(g + b) - 1 + lead;  // aligned-window position of particle g[b] - 1
     h = h < lead ? (int64_t)lead : (h > PA - 1 ? PA - 1 : h);
-    const int lo = (int)(h / tile);
+    static_assert((1 << kLocalBits) == kTileMax, "full tiles are 2^kLocalBits elements");
+    const int lo = tile == kTileMax ? (int)((uint64_t)h >> kLocalBits) : (int)(h / tile);
     const bool good = boundary_at_or_below(table[lo], th, tl) &&
                       (lo + 1 >= T || !boundary_at_or_below(table[lo + 1], th, tl)) && table[lo].il >= 0;
     const TableEntry e = table[lo];
