@@ -120,17 +120,24 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str):
-    """dram bytes per launch recorded by the committed ncu summary, if the kernel's
-    sources have not changed since."""
+def profiled_entry(kernel: str):
+    """The kernel's counters recorded by the committed ncu summary, if its sources
+    have not changed since (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
-            d = json.load(fh)
-        e = d[kernel]
-        if source_hash(e["sources"]) != e["source_hash"]:
-            return None
-        return float(e["dram_bytes_per_launch"]) * float(e.get("scale_to_bench", 1.0))
+            e = json.load(fh)[kernel]
+        return e if source_hash(e["sources"]) == e["source_hash"] else None
+    except Exception:
+        return None
+
+
+def profiled_traffic(kernel: str):
+    """dram bytes per launch recorded by the committed ncu summary, if the kernel's
+    sources have not changed since."""
+    e = profiled_entry(kernel)
+    try:
+        return None if e is None else float(e["dram_bytes_per_launch"]) * float(e.get("scale_to_bench", 1.0))
     except Exception:
         return None
 
@@ -343,6 +350,22 @@ def run_gpu(args):
                          "note": "one random 4-byte log-weight read (a 32-byte L2 sector) per chain step; the "
                                  "array is L2-resident, so neither HBM bandwidth nor ALU throughput bounds the "
                                  "chains: the SMs issue about one such sector request per cycle"})
+        # the probe's rate against figures that do not come from the probe: one
+        # sector request per SM per cycle at this run's SM clock, and ncu's own
+        # L1TEX and L2 throughput for the kernel (committed capture)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = (clocks or {}).get("sm_mhz")
+        ent = profiled_entry("metropolis") or {}
+        check = {"sm_count": n_sm, "sm_mhz": sm_mhz,
+                 "ncu_l1tex_pct_of_peak": ent.get("l1tex_pct_of_peak"),
+                 "ncu_lts_pct_of_peak": ent.get("lts_pct_of_peak"),
+                 "ncu_l2_hit_pct": ent.get("l2_hit_pct")}
+        if sm_mhz:
+            unit_rate = n_sm * sm_mhz * 1e6
+            check.update({"one_request_per_sm_cycle_per_s": round(unit_rate, 1),
+                          "probe_over_that_rate": round(l2_rate / unit_rate, 4),
+                          "kernel_over_that_rate": round(steps_per_s / unit_rate, 4)})
+        roofline["peak_check"] = check
     headline = breakdown["systematic"]
 
     e2e = run_e2e(args, pf, torch, dev, stream, lw_h, st_h, P, row_bytes) if not args.no_e2e else None
