@@ -92,12 +92,13 @@ enum {
  * systematic, stratified or multinomial call resamples in one cooperative
  * launch (4096 tiles of 8192 log-weights).  Beyond it the call runs three
  * ordinary launches on the stream -- the tile scans, one CTA forming every
- * tile's exact carry, then the assignment (systematic, stratified: the tiles
- * scanned again) or, for the multinomial, a guide table and the draws (each
- * through its guide entry and one window of the stored cumulative weights,
- * else binary searches over the tile table and the tile) -- with the same
- * tiles, boundaries and per-tile arithmetic, and workspace scratch of about
- * 48 bytes per 8192 particles (multinomial: 5 bytes per particle more).  A
+ * tile's exact carry, then the assignment (systematic, stratified: from the
+ * tiles' stored cumulative weights) or, for the multinomial, a guide table
+ * and the draws (each through its guide entry and one window of the stored
+ * cumulative weights, else binary searches over the tile table and the tile)
+ * -- with the same tiles, boundaries and per-tile arithmetic, and workspace
+ * scratch of 4 bytes per particle plus about 48 bytes per 8192 (multinomial:
+ * 1 byte per particle more, its guide table).  A
  * multinomial call also takes these launches from about 3300 tiles on, where
  * its tile table and samples no longer fit shared memory. */
 #define PF_MAX_CUMULATIVE (1LL << 25)

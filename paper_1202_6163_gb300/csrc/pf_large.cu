@@ -3,15 +3,17 @@
 // 2^31 - 1 particles.  Three ordinary launches in stream order, with no wait of
 // one CTA on another:
 //   1. k_large_scan: tiles of 8192 log-weights, grid-stride: the tile scan
-//      (pf_tile.cuh) and a 16-byte record (k_t, S_t, i_last); the multinomial
-//      also keeps each tile's cumulative weights v_i;
+//      (pf_tile.cuh), a 16-byte record (k_t, S_t, i_last) and the tile's
+//      cumulative weights v_i (sign bit: zero weight);
 //   2. k_large_carries: one CTA: the largest tile exponent K and the exact
 //      exclusive prefix B_t = sum_{t' < t} S_t' 2^{k_t' - K} of every tile
 //      (128-bit fixed point; each thread a contiguous run of records, then one
 //      block scan of the run totals), W = B_T, and the multinomial's tile table;
 //   3. k_large_assign (systematic, stratified): grid-stride over tiles: the
-//      tile scan again, the tile's offset map from B_t and B_{t+1}, the offsets
-//      and their run-length decode (pf_assign.cuh).  Multinomial: k_large_guide
+//      tile's v_i read back (not rescanned: 6-7% faster at 2^25 - 2^27 for the
+//      extra 4 B written and read per particle), the tile's offset map from B_t
+//      and B_{t+1}, the offsets and their run-length decode (pf_assign.cuh).
+//      Multinomial: k_large_guide
 //      decodes the guide table (the first particle above each of P/4 evenly
 //      spaced targets) from the stored v_i, then k_large_draws runs the draws,
 //      each through its guide entry and one window of v_i, or, where that does
@@ -38,7 +40,6 @@ struct LargeScalars {
 };
 
 struct LargeShared {
-    TileShared tile;
     AssignShared as;
     TileMap map;
     int pad;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_large_scan(SortedParams p, uint
         const int n = (int)min((int64_t)kLargeTile, PA - t0);
         const TileSummary ts = tile_scan_k<16>(p.lw + t0, t == 0 ? p.lead : 0, n, sm, th);
         if (ts.bad && threadIdx.x == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
-        if (KIND == KIND_MULTI) write_tile_v<16>(p, th, t0, n);
+        write_tile_v<16>(p, th, t0, n);  // read back by launch 3
         if (threadIdx.x == 0)
             rec[t] = make_uint4((uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo),
                                 (uint32_t)ts.i_last);
@@ -159,12 +160,13 @@ __global__ void __launch_bounds__(kThreads) k_large_carries(SortedParams p, cons
 }
 
 // ---------------------------------------------------------------------------
-// Launch 3, systematic / stratified: each tile scanned again, its offset map
-// from its two boundaries (the same function of a boundary for both ends, so
-// neighbouring tiles share their end exactly), then its offsets decoded.
+// Launch 3, systematic / stratified: each tile's stored cumulative weights and
+// record read back, its offset map from its two boundaries (the same function
+// of a boundary for both ends, so neighbouring tiles share their end exactly),
+// then its offsets decoded.
 // ---------------------------------------------------------------------------
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 2) k_large_assign(SortedParams p, const i128* bnd,
+__global__ void __launch_bounds__(kThreads, 2) k_large_assign(SortedParams p, const uint4* rec, const i128* bnd,
                                                               const LargeScalars* sc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LargeShared& sm = *reinterpret_cast<LargeShared*>(smem_raw);
@@ -185,7 +187,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_large_assign(SortedParams p, co
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
         const int64_t t0 = (int64_t)t * kLargeTile;
         const int n = (int)min((int64_t)kLargeTile, PA - t0);
-        const TileSummary ts = tile_scan_k<16>(p.lw + t0, t == 0 ? p.lead : 0, n, sm.tile, th);
+        read_tile_v<16>(p.v_out + t0, n, th);
+        const uint4 r = rec[t];
+        TileSummary ts;
+        ts.k = (int)r.x;
+        ts.i_last = (int)r.w;
+        ts.bad = 0;
+        ts.S = {__uint_as_float(r.y), __uint_as_float(r.z)};
         if (tid < 32) {  // lanes 0 and 1 form the map (the other pairs of warp 0 the same one)
             const TileMap m = tile_map_pair<KIND>(p, sm.as, bnd[t], bnd[t + 1], ts.k, 0xffffffffu);
             if (tid == 0) sm.map = m;
@@ -308,7 +316,7 @@ LargeLayout large_layout(int kind, int64_t PA) {
     l.table = align256(l.bnd + (T + 1) * sizeof(i128));
     l.scalars = align256(l.table + (multi ? T * sizeof(TableEntry) : 0));
     l.v = align256(l.scalars + sizeof(LargeScalars));
-    l.g = align256(l.v + (multi ? (size_t)PA * sizeof(float) : 0));
+    l.g = align256(l.v + (size_t)PA * sizeof(float));
     l.total = l.g + (multi ? (size_t)guide_buckets(PA) * sizeof(int32_t) : 0);
     return l;
 }
@@ -324,7 +332,7 @@ cudaError_t launch_large_kind(SortedParams p, unsigned char* scratch, int num_sm
     i128* bnd = reinterpret_cast<i128*>(scratch + l.bnd);
     TableEntry* table = reinterpret_cast<TableEntry*>(scratch + l.table);
     LargeScalars* sc = reinterpret_cast<LargeScalars*>(scratch + l.scalars);
-    if (KIND == KIND_MULTI) p.v_out = reinterpret_cast<float*>(scratch + l.v);
+    p.v_out = reinterpret_cast<float*>(scratch + l.v);
     const int grid = T < 2 * num_sms ? T : 2 * num_sms;  // two resident CTAs per SM, grid-stride over tiles
     k_large_scan<KIND><<<grid, kThreads, 0, s>>>(p, rec);
     cudaError_t e = cudaGetLastError();
@@ -349,7 +357,7 @@ cudaError_t launch_large_kind(SortedParams p, unsigned char* scratch, int num_sm
         if (gd > (int64_t)num_sms * 16) gd = (int64_t)num_sms * 16;
         k_large_draws<true><<<(unsigned)gd, kThreads, 0, s>>>(p, table, sc, g, M);
     } else {
-        k_large_assign<KIND><<<grid, kThreads, kAssignSmem, s>>>(p, bnd, sc);
+        k_large_assign<KIND><<<grid, kThreads, kAssignSmem, s>>>(p, rec, bnd, sc);
     }
     return cudaGetLastError();
 }
