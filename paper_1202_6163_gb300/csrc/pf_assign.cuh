@@ -830,8 +830,9 @@ __device__ __forceinline__ void write_tile_samples(const TileThread& th, int n, 
 
 // Reloads a tile stored by write_tile_v into th (elements of tile-local
 // indices [0, n)): v from the magnitudes, the positive-weight mask from the
-// sign bits.  Slots at or beyond n are not read.
-template <int KK = 0>  // elements per thread when fixed (the tile was scanned with KK), 0 = from n
+// sign bits.  Slots at or beyond n are not read.  SMEM: vg0 is a copy of the
+// tile in shared memory.
+template <int KK = 0, bool SMEM = false>  // KK: elements per thread when fixed (the tile was scanned with KK), 0 = from n
 __device__ __forceinline__ void read_tile_v(const float* vg0, int n, TileThread& th) {
     const int K = KK ? KK : per_thread_count(n);
     th.K = K;
@@ -843,14 +844,16 @@ __device__ __forceinline__ void read_tile_v(const float* vg0, int n, TileThread&
         if (4 * q < K) {
             float o[4];
             if (th.e0 + 4 * q + 3 < n) {
-                const float4 t = __ldcg(reinterpret_cast<const float4*>(vg + 4 * q));
+                const float4 t = SMEM ? *reinterpret_cast<const float4*>(vg + 4 * q)
+                                      : __ldcg(reinterpret_cast<const float4*>(vg + 4 * q));
                 o[0] = t.x;
                 o[1] = t.y;
                 o[2] = t.z;
                 o[3] = t.w;
             } else {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) o[r] = th.e0 + 4 * q + r < n ? __ldcg(vg + 4 * q + r) : -0.0f;
+                for (int r = 0; r < 4; ++r)
+                    o[r] = th.e0 + 4 * q + r < n ? (SMEM ? vg[4 * q + r] : __ldcg(vg + 4 * q + r)) : -0.0f;
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {

@@ -2,8 +2,9 @@
 // schemes (Section 2, Figure 1a-c) for P + lead > PF_MAX_CUMULATIVE, up to
 // 2^31 - 1 particles.  Three ordinary launches in stream order, with no wait of
 // one CTA on another:
-//   1. k_large_scan: tiles of 8192 log-weights, grid-stride: the tile scan
-//      (pf_tile.cuh), a 16-byte record (k_t, S_t, i_last) and the tile's
+//   1. k_large_scan: tiles of 8192 log-weights, grid-stride, each bulk-copied
+//      into shared memory while the CTA's previous tile is scanned: the tile
+//      scan (pf_tile.cuh), a 16-byte record (k_t, S_t, i_last) and the tile's
 //      cumulative weights v_i (sign bit: zero weight);
 //   2. k_large_carries: one CTA: the largest tile exponent K and the exact
 //      exclusive prefix B_t = sum_{t' < t} S_t' 2^{k_t' - K} of every tile
@@ -11,8 +12,9 @@
 //      block scan of the run totals), W = B_T, and the multinomial's tile table;
 //   3. k_large_assign (systematic, stratified): grid-stride over tiles: the
 //      tile's v_i read back (not rescanned: 6-7% faster at 2^25 - 2^27 for the
-//      extra 4 B written and read per particle), the tile's offset map from B_t
-//      and B_{t+1}, the offsets and their run-length decode (pf_assign.cuh).
+//      extra 4 B written and read per particle; bulk-copied into shared memory
+//      while the previous tile is assigned), the tile's offset map from B_t and
+//      B_{t+1}, the offsets and their run-length decode (pf_assign.cuh).
 //      Multinomial: k_large_guide
 //      decodes the guide table (the first particle above each of P/4 evenly
 //      spaced targets) from the stored v_i, then k_large_draws runs the draws,
@@ -42,7 +44,7 @@ struct LargeScalars {
 struct LargeShared {
     AssignShared as;
     TileMap map;
-    int pad;
+    uint64_t bar;  // the assignment's tile copies
 };
 static_assert(sizeof(LargeShared) % 16 == 0, "the staging buffers are 16-byte aligned");
 
@@ -56,23 +58,63 @@ __device__ __forceinline__ i128 record_mass(uint4 r, int K) {
 }
 
 // ---------------------------------------------------------------------------
-// Launch 1: the tile scans.
+// Launch 1: the tile scans.  A CTA's tiles are t = blockIdx.x + r gridDim.x;
+// tile r + 1 is bulk-copied into one of two shared-memory buffers while tile r
+// is scanned from the other.
 // ---------------------------------------------------------------------------
+struct ScanShared {
+    TileShared tile;
+    uint64_t bar[2];
+};
+constexpr size_t kScanSmem = ((sizeof(ScanShared) + 15) & ~(size_t)15) + 2 * (size_t)kLargeTile * sizeof(float);
+
+// Thread 0: the copy of this CTA's tile r (its whole 16-byte pieces) into buf,
+// completing on bar.
+__device__ __forceinline__ void issue_tile_copy(const float* src, int64_t PA, int r, float* buf, uint64_t* bar) {
+    const int64_t t0 = (int64_t)(blockIdx.x + (int64_t)r * gridDim.x) * kLargeTile;
+    const uint32_t bytes = (uint32_t)((int)min((int64_t)kLargeTile, PA - t0) & ~3) * 4u;
+    if (bytes) bulk_load(buf, src + t0, bytes, bar);
+    else mbar_arrive(bar);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2) k_large_scan(SortedParams p, uint4* rec) {
-    __shared__ TileShared sm;
-    TileThread th;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScanShared& sm = *reinterpret_cast<ScanShared*>(smem_raw);
+    float* slot = reinterpret_cast<float*>(smem_raw + ((sizeof(ScanShared) + 15) & ~(size_t)15));
+    const int tid = threadIdx.x;
     const int64_t PA = p.P + p.lead;
-    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
+    const int n_mine = (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // grid <= tiles
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) issue_tile_copy(p.lw, PA, 0, slot, &sm.bar[0]);
+    const uint64_t t_start = global_ns();
+    TileThread th;
+    for (int r = 0; r < n_mine; ++r) {
+        const int t = (int)blockIdx.x + r * (int)gridDim.x;
         const int64_t t0 = (int64_t)t * kLargeTile;
         const int n = (int)min((int64_t)kLargeTile, PA - t0);
-        const TileSummary ts = tile_scan_k<16>(p.lw + t0, t == 0 ? p.lead : 0, n, sm, th);
-        if (ts.bad && threadIdx.x == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
+        if (tid == 0 && r + 1 < n_mine)
+            issue_tile_copy(p.lw, PA, r + 1, slot + ((r + 1) & 1) * kLargeTile, &sm.bar[(r + 1) & 1]);
+        // a copy not complete within the wait limit is reported (the results
+        // are then unspecified)
+        if (!mbar_wait(&sm.bar[r & 1], (uint32_t)(r >> 1) & 1u, t_start, p.wait_ns) && tid == 0)
+            set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
+        // a ragged last tile: its tail is not in the copy; read it from global memory
+        const int lo = t == 0 ? p.lead : 0;
+        const TileSummary ts = (n & 3) == 0 ? tile_scan_k<16, true>(slot + (r & 1) * kLargeTile, lo, n, sm.tile, th)
+                                            : tile_scan_k<16>(p.lw + t0, lo, n, sm.tile, th);
+        if (ts.bad && tid == 0) set_status(p.ctl + CTL_STATUS, ST_DOMAIN);
         write_tile_v<16>(p, th, t0, n);  // read back by launch 3
-        if (threadIdx.x == 0)
+        if (tid == 0)
             rec[t] = make_uint4((uint32_t)ts.k, __float_as_uint(ts.bad ? NAN : ts.S.hi), __float_as_uint(ts.S.lo),
                                 (uint32_t)ts.i_last);
-        __syncthreads();  // the tile scan's shared fields are reused by the next tile
+        fence_proxy_async_smem();  // this tile's reads of its buffer before the buffer's next copy
+        __syncthreads();           // and the tile scan's shared fields are reused by the next tile
     }
 }
 
@@ -171,36 +213,51 @@ __global__ void __launch_bounds__(kThreads, 2) k_large_assign(SortedParams p, co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LargeShared& sm = *reinterpret_cast<LargeShared*>(smem_raw);
     int32_t* stage = reinterpret_cast<int32_t*>(smem_raw + sizeof(LargeShared));
+    float* vbuf = reinterpret_cast<float*>(stage + 2 * kIoCap);  // one tile's stored cumulative weights
     const int tid = threadIdx.x;
     if (!sc->ok) return;  // launch 2 recorded a domain error
+    const int64_t PA = p.P + p.lead;
+    const int n_mine = (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // grid <= tiles
     if (tid == 0) {
         sm.as.Wt = sc->Wt;
         sm.as.K = sc->K;
         sm.as.W_hi = sc->W_hi;
         sm.as.W_lo = sc->W_lo;
+        mbar_init(&sm.bar, 1);
+        fence_mbar_init();
     }
     stage_init<kIoCap>(stage);
     __syncthreads();
-    const int64_t PA = p.P + p.lead;
+    // tile r + 1's copy is issued once every thread has taken tile r out of the
+    // buffer, and lands while tile r is assigned
+    if (tid == 0) issue_tile_copy(p.v_out, PA, 0, vbuf, &sm.bar);
+    const uint64_t t_start = global_ns();
     uint32_t chunks = 0;  // staging chunks decoded by this CTA
     TileThread th;
-    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
+    for (int r = 0; r < n_mine; ++r) {
+        const int t = (int)blockIdx.x + r * (int)gridDim.x;
         const int64_t t0 = (int64_t)t * kLargeTile;
         const int n = (int)min((int64_t)kLargeTile, PA - t0);
-        read_tile_v<16>(p.v_out + t0, n, th);
-        const uint4 r = rec[t];
+        if (!mbar_wait(&sm.bar, (uint32_t)r & 1u, t_start, p.wait_ns) && tid == 0)
+            set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);  // the results are then unspecified
+        // a ragged last tile: its tail is not in the copy; read it from global memory
+        if ((n & 3) == 0) read_tile_v<16, true>(vbuf, n, th);
+        else read_tile_v<16>(p.v_out + t0, n, th);
+        const uint4 rc = rec[t];
         TileSummary ts;
-        ts.k = (int)r.x;
-        ts.i_last = (int)r.w;
+        ts.k = (int)rc.x;
+        ts.i_last = (int)rc.w;
         ts.bad = 0;
-        ts.S = {__uint_as_float(r.y), __uint_as_float(r.z)};
+        ts.S = {__uint_as_float(rc.y), __uint_as_float(rc.z)};
         if (tid < 32) {  // lanes 0 and 1 form the map (the other pairs of warp 0 the same one)
             const TileMap m = tile_map_pair<KIND>(p, sm.as, bnd[t], bnd[t + 1], ts.k, 0xffffffffu);
             if (tid == 0) sm.map = m;
         }
+        fence_proxy_async_smem();  // this thread's reads of the buffer before its next copy
         __syncthreads();
+        if (tid == 0 && r + 1 < n_mine) issue_tile_copy(p.v_out, PA, r + 1, vbuf, &sm.bar);
         assign_offspring<KIND, 16, kIoCap>(p, sm.as, sm.map, stage, chunks, th, ts, t0 - p.lead);
-        __syncthreads();  // the map and the tile scan's shared fields are reused by the next tile
+        __syncthreads();  // the map is reused by the next tile
     }
 }
 
@@ -321,7 +378,8 @@ LargeLayout large_layout(int kind, int64_t PA) {
     return l;
 }
 
-constexpr size_t kAssignSmem = sizeof(LargeShared) + 2 * (size_t)kIoCap * sizeof(int32_t);
+constexpr size_t kGuideSmem = sizeof(LargeShared) + 2 * (size_t)kIoCap * sizeof(int32_t);
+constexpr size_t kAssignSmem = kGuideSmem + (size_t)kLargeTile * sizeof(float);  // and one tile's copy
 
 template <int KIND>
 cudaError_t launch_large_kind(SortedParams p, unsigned char* scratch, int num_sms, cudaStream_t s) {
@@ -334,7 +392,7 @@ cudaError_t launch_large_kind(SortedParams p, unsigned char* scratch, int num_sm
     LargeScalars* sc = reinterpret_cast<LargeScalars*>(scratch + l.scalars);
     p.v_out = reinterpret_cast<float*>(scratch + l.v);
     const int grid = T < 2 * num_sms ? T : 2 * num_sms;  // two resident CTAs per SM, grid-stride over tiles
-    k_large_scan<KIND><<<grid, kThreads, 0, s>>>(p, rec);
+    k_large_scan<KIND><<<grid, kThreads, kScanSmem, s>>>(p, rec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_large_carries<KIND><<<1, kThreads, 0, s>>>(p, rec, bnd, table, sc);
@@ -349,7 +407,7 @@ cudaError_t launch_large_kind(SortedParams p, unsigned char* scratch, int num_sm
         pg.P = M;
         pg.Pd = (double)M;
         pg.guide = 1;
-        k_large_guide<<<grid, kThreads, kAssignSmem, s>>>(pg, PA, rec, bnd, sc);
+        k_large_guide<<<grid, kThreads, kGuideSmem, s>>>(pg, PA, rec, bnd, sc);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int64_t nq = (p.P + 3) >> 2;
@@ -363,8 +421,8 @@ cudaError_t launch_large_kind(SortedParams p, unsigned char* scratch, int num_sm
 }
 }  // namespace
 
-// Once per device: the assignment kernels' staging buffers exceed the default
-// dynamic shared-memory limit.
+// Once per device: the scans' tile buffers and the assignment kernels' staging
+// buffers exceed the default dynamic shared-memory limit.
 cudaError_t prepare_large() {
     cudaError_t e = cudaFuncSetAttribute(k_large_assign<KIND_SYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kAssignSmem);
@@ -372,7 +430,13 @@ cudaError_t prepare_large() {
         e = cudaFuncSetAttribute(k_large_assign<KIND_STRAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kAssignSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_large_guide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAssignSmem);
+        e = cudaFuncSetAttribute(k_large_guide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGuideSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_large_scan<KIND_MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_large_scan<KIND_STRAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_large_scan<KIND_SYS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem);
     return e;
 }
 
