@@ -30,3 +30,31 @@ def test_reference_arm_json_line():
     assert d["ms_per_step"] * d["steps"] / 1e3 <= d["cpu_baseline"]["seconds_measured"] * 1.01 + 1e-3
     assert d["cpu_baseline"]["seconds_measured"] <= wall
     assert d["ms_per_step_full_P_estimate"] >= d["ms_per_step"]
+
+
+def test_profiled_counters_follow_their_sources(tmp_path, monkeypatch):
+    """The roofline's committed counters (profiles/traffic.json) are used only while
+    the hash of the kernel's sources matches the captured build."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        d = json.load(fh)
+    e = d["metropolis"]
+    for k in ("sources", "source_hash", "dram_bytes_per_launch", "l1tex_pct_of_peak", "lts_pct_of_peak",
+              "l2_hit_pct"):
+        assert k in e, k
+    if bench.source_hash(e["sources"]) == e["source_hash"]:
+        assert bench.profiled_entry("metropolis")["l1tex_pct_of_peak"] == e["l1tex_pct_of_peak"]
+        assert bench.profiled_traffic("metropolis") == float(e["dram_bytes_per_launch"])
+    # a copy whose hash no longer matches its sources gives nothing
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    for s in e["sources"]:
+        dst = root / s
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        with open(os.path.join(ROOT, s), "rb") as fh:
+            dst.write_bytes(fh.read() + b"\n// changed\n")
+    (root / "profiles" / "traffic.json").write_text(json.dumps({"metropolis": e}))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.profiled_entry("metropolis") is None
+    assert bench.profiled_traffic("metropolis") is None
