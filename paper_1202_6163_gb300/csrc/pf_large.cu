@@ -92,7 +92,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_large_scan(SortedParams p, uint
     }
     __syncthreads();
     if (tid == 0) issue_tile_copy(p.lw, PA, 0, slot, &sm.bar[0]);
-    const uint64_t t_start = global_ns();
     TileThread th;
     for (int r = 0; r < n_mine; ++r) {
         const int t = (int)blockIdx.x + r * (int)gridDim.x;
@@ -100,9 +99,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_large_scan(SortedParams p, uint
         const int n = (int)min((int64_t)kLargeTile, PA - t0);
         if (tid == 0 && r + 1 < n_mine)
             issue_tile_copy(p.lw, PA, r + 1, slot + ((r + 1) & 1) * kLargeTile, &sm.bar[(r + 1) & 1]);
-        // a copy not complete within the wait limit is reported (the results
-        // are then unspecified)
-        if (!mbar_wait(&sm.bar[r & 1], (uint32_t)(r >> 1) & 1u, t_start, p.wait_ns) && tid == 0)
+        // a copy not complete within the wait limit (from this wait's start) is
+        // reported; the results are then unspecified
+        if (!mbar_wait(&sm.bar[r & 1], (uint32_t)(r >> 1) & 1u, global_ns(), p.wait_ns) && tid == 0)
             set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
         // a ragged last tile: its tail is not in the copy; read it from global memory
         const int lo = t == 0 ? p.lead : 0;
@@ -231,15 +230,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_large_assign(SortedParams p, co
     // tile r + 1's copy is issued once every thread has taken tile r out of the
     // buffer, and lands while tile r is assigned
     if (tid == 0) issue_tile_copy(p.v_out, PA, 0, vbuf, &sm.bar);
-    const uint64_t t_start = global_ns();
     uint32_t chunks = 0;  // staging chunks decoded by this CTA
     TileThread th;
     for (int r = 0; r < n_mine; ++r) {
         const int t = (int)blockIdx.x + r * (int)gridDim.x;
         const int64_t t0 = (int64_t)t * kLargeTile;
         const int n = (int)min((int64_t)kLargeTile, PA - t0);
-        if (!mbar_wait(&sm.bar, (uint32_t)r & 1u, t_start, p.wait_ns) && tid == 0)
-            set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);  // the results are then unspecified
+        // bounded from this wait's start; the results are then unspecified
+        if (!mbar_wait(&sm.bar, (uint32_t)r & 1u, global_ns(), p.wait_ns) && tid == 0)
+            set_status(p.ctl + CTL_STATUS, ST_TIMEOUT);
         // a ragged last tile: its tail is not in the copy; read it from global memory
         if ((n & 3) == 0) read_tile_v<16, true>(vbuf, n, th);
         else read_tile_v<16>(p.v_out + t0, n, th);
