@@ -15,11 +15,11 @@
 //      extra 4 B written and read per particle; bulk-copied into shared memory
 //      while the previous tile is assigned), the tile's offset map from B_t and
 //      B_{t+1}, the offsets and their run-length decode (pf_assign.cuh).
-//      Multinomial: k_large_guide
-//      decodes the guide table (the first particle above each of P/4 evenly
-//      spaced targets) from the stored v_i, then k_large_draws runs the draws,
-//      each through its guide entry and one window of v_i, or, where that does
-//      not settle it, by binary searches over the tile table and the tile's v_i.
+//      Multinomial: k_large_guide decodes the guide table (the first particle
+//      above each of P/4 evenly spaced targets) from the stored v_i, then
+//      k_large_draws runs the draws, each through its guide entry and one
+//      window of v_i, or, where that does not settle it, by binary searches over
+//      the tile table and the tile's v_i.
 // The tiles, the exact boundaries and the per-tile arithmetic are those of the
 // single-launch kernels, so the results follow the same rules.  A NaN/+inf or
 // all-zero weight set records PF_ERR_DOMAIN in launch 1 or 2, and launch 3
